@@ -1,0 +1,314 @@
+/*
+ * FP64 CPU oracle for voxel-driven cone-beam back-projection.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * definition that the CUDA library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may load it; the product
+ * path never does.  It shares no code, header or constant with the CUDA
+ * library.
+ *
+ * What it computes (Sec. IV, Listing 1 of Hofmann et al., "Performance
+ * Engineering for a Medical Imaging Application on the Intel Xeon Phi
+ * Accelerator"): for every projection k and every voxel (x, y, z)
+ *   X = origin + (x, y, z) * voxel_size                   world coordinates
+ *   (u', v', w) = P_k (X, 1)                              forward projection
+ *   u = u'/w, v = v'/w                                    dehomogenisation
+ *   i = floor(u), j = floor(v), a = u - i, b = v - j      cell and weights
+ *   p(m, n) = I_k[n*W + m] inside the detector, else 0    four taps
+ *   val = (1-b)((1-a)p(i,j) + a p(i+1,j)) + b((1-a)p(i,j+1) + a p(i+1,j+1))
+ *   f[z][y][x] += val / w^2                               inverse-square weight
+ * in double precision, views in index order, the volume accumulated (+=).
+ *
+ * Readings of the listing where it is silent or garbled:
+ *  - P_k is row-major 3x4 (the listing stores it column-major);
+ *  - the bounds are 0 <= m < W (columns, u) and 0 <= n < H (rows, v); the
+ *    listing swaps the names width/height in its tests but addresses the
+ *    image as iiy*width + iix;
+ *  - float to int is floor (the listing's (int) cast truncates, which only
+ *    differs for u or v in (-1, 0)); literal_trunc = 1 selects truncation;
+ *  - a voxel with w <= 0 (behind the source) contributes nothing;
+ *  - integer (u, v) is the centre of pixel (u, v).
+ *
+ * Parity pins live in the tests: constant projections (closed form
+ * c * sum_k 1/w_k^2), an orthographic matrix that copies the image into the
+ * volume, brute-force tent sums, linearity, scale, view chunking, view
+ * permutation, the adjoint dot product and the thread split.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_MAX_THREADS 1024
+
+/* One voxel against one view: detector cell (i, j), weights (a, b) and
+ * 1/w^2.  Returns 0 when the voxel contributes nothing: w <= 0 (behind the
+ * source), or all four taps outside the W x H image (then every tap reads
+ * zero, so skipping is exact and keeps the int64 conversion defined). */
+static int oracle_cell(const double P[12], double X, double Y, double Z, int64_t W, int64_t H,
+                       int literal_trunc, int64_t *i, int64_t *j, double *a, double *b,
+                       double *inv_w2)
+{
+    double up = P[0] * X + P[1] * Y + P[2] * Z + P[3];
+    double vp = P[4] * X + P[5] * Y + P[6] * Z + P[7];
+    double w = P[8] * X + P[9] * Y + P[10] * Z + P[11];
+    if (!(w > 0.0)) return 0;
+    double u = up / w;
+    double v = vp / w;
+    double fu = literal_trunc ? trunc(u) : floor(u);
+    double fv = literal_trunc ? trunc(v) : floor(v);
+    if (!(fu >= -1.0 && fu < (double)W && fv >= -1.0 && fv < (double)H)) return 0;
+    *i = (int64_t)fu;
+    *j = (int64_t)fv;
+    *a = u - fu;
+    *b = v - fv;
+    *inv_w2 = 1.0 / (w * w);
+    return 1;
+}
+
+static double oracle_tap(const float *img, int64_t W, int64_t H, int64_t m, int64_t n)
+{
+    if (m < 0 || m >= W || n < 0 || n >= H) return 0.0;
+    return (double)img[n * W + m];
+}
+
+typedef struct {
+    double *vol;
+    const float *proj;
+    const float *mats;
+    int64_t nx, ny, nz, W, H, n_views;
+    double vs[3], org[3];
+    int literal_trunc;
+    int64_t line_begin, line_end;   /* collapsed (z, y) lines owned by this worker */
+} bp_job;
+
+static void *bp_worker(void *arg)
+{
+    bp_job *jb = (bp_job *)arg;
+    const int64_t plane = jb->W * jb->H;
+    for (int64_t k = 0; k < jb->n_views; ++k) {
+        double P[12];
+        for (int q = 0; q < 12; ++q) P[q] = (double)jb->mats[k * 12 + q];
+        const float *img = jb->proj + k * plane;
+        for (int64_t line = jb->line_begin; line < jb->line_end; ++line) {
+            int64_t z = line / jb->ny, y = line % jb->ny;
+            double Z = jb->org[2] + (double)z * jb->vs[2];
+            double Y = jb->org[1] + (double)y * jb->vs[1];
+            double *row = jb->vol + (z * jb->ny + y) * jb->nx;
+            for (int64_t x = 0; x < jb->nx; ++x) {
+                double X = jb->org[0] + (double)x * jb->vs[0];
+                int64_t i, j;
+                double a, b, iw2;
+                if (!oracle_cell(P, X, Y, Z, jb->W, jb->H, jb->literal_trunc, &i, &j, &a, &b, &iw2)) continue;
+                double p00 = oracle_tap(img, jb->W, jb->H, i, j);
+                double p10 = oracle_tap(img, jb->W, jb->H, i + 1, j);
+                double p01 = oracle_tap(img, jb->W, jb->H, i, j + 1);
+                double p11 = oracle_tap(img, jb->W, jb->H, i + 1, j + 1);
+                double lo = (1.0 - a) * p00 + a * p10;
+                double hi = (1.0 - a) * p01 + a * p11;
+                double val = (1.0 - b) * lo + b * hi;
+                row[x] += val * iw2;
+            }
+        }
+    }
+    return NULL;
+}
+
+static int check_geom(const int64_t dims[3], int64_t W, int64_t H, int64_t n_views)
+{
+    if (!dims || dims[0] < 0 || dims[1] < 0 || dims[2] < 0) return -1;
+    if (W <= 0 || H <= 0 || n_views < 0) return -1;
+    return 0;
+}
+
+/* Back-project n_views projections into vol (nz, ny, nx) doubles, +=.
+ * The thread split is over collapsed (z, y) lines in equal static chunks,
+ * as the paper's OpenMP collapse(z, y) schedule (Sec. VI); every voxel still
+ * sums its views in index order, so any nthreads gives the same bits. */
+int oracle_backproject(double *vol, const int64_t dims[3], const double voxel_size[3],
+                       const double origin[3], const float *proj, int64_t W, int64_t H,
+                       const float *mats, int64_t n_views, int nthreads, int literal_trunc)
+{
+    if (check_geom(dims, W, H, n_views)) return -1;
+    int64_t lines = dims[1] * dims[2];
+    if (lines == 0 || dims[0] == 0 || n_views == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > ORACLE_MAX_THREADS) nthreads = ORACLE_MAX_THREADS;
+    if (nthreads > lines) nthreads = (int)lines;
+    bp_job *jobs = (bp_job *)calloc((size_t)nthreads, sizeof(bp_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int t = 0; t < nthreads; ++t) {
+        bp_job *jb = &jobs[t];
+        jb->vol = vol; jb->proj = proj; jb->mats = mats;
+        jb->nx = dims[0]; jb->ny = dims[1]; jb->nz = dims[2];
+        jb->W = W; jb->H = H; jb->n_views = n_views;
+        for (int q = 0; q < 3; ++q) { jb->vs[q] = voxel_size[q]; jb->org[q] = origin[q]; }
+        jb->literal_trunc = literal_trunc;
+        jb->line_begin = lines * t / nthreads;
+        jb->line_end = lines * (t + 1) / nthreads;
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, bp_worker, &jobs[t]) != 0) break;
+        started = t;
+    }
+    bp_worker(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    /* if a thread failed to start, do its lines here (same per-voxel order) */
+    for (int t = started + 1; t < nthreads; ++t) bp_worker(&jobs[t]);
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* Back-project into a list of voxels only: out[q] += f at voxel
+ * (xyz[3q], xyz[3q+1], xyz[3q+2]).  Same arithmetic as oracle_backproject,
+ * used to check sampled voxels of volumes too large for the full oracle. */
+int oracle_backproject_voxels(double *out, const int64_t *xyz, int64_t n_vox,
+                              const double voxel_size[3], const double origin[3],
+                              const float *proj, int64_t W, int64_t H, const float *mats,
+                              int64_t n_views)
+{
+    if (W <= 0 || H <= 0 || n_views < 0 || n_vox < 0) return -1;
+    const int64_t plane = W * H;
+    for (int64_t q = 0; q < n_vox; ++q) {
+        double X = origin[0] + (double)xyz[3 * q + 0] * voxel_size[0];
+        double Y = origin[1] + (double)xyz[3 * q + 1] * voxel_size[1];
+        double Z = origin[2] + (double)xyz[3 * q + 2] * voxel_size[2];
+        double acc = out[q];
+        for (int64_t k = 0; k < n_views; ++k) {
+            double P[12];
+            for (int c = 0; c < 12; ++c) P[c] = (double)mats[k * 12 + c];
+            int64_t i, j;
+            double a, b, iw2;
+            if (!oracle_cell(P, X, Y, Z, W, H, 0, &i, &j, &a, &b, &iw2)) continue;
+            const float *img = proj + k * plane;
+            double lo = (1.0 - a) * oracle_tap(img, W, H, i, j) + a * oracle_tap(img, W, H, i + 1, j);
+            double hi = (1.0 - a) * oracle_tap(img, W, H, i, j + 1) + a * oracle_tap(img, W, H, i + 1, j + 1);
+            acc += ((1.0 - b) * lo + b * hi) * iw2;
+        }
+        out[q] = acc;
+    }
+    return 0;
+}
+
+typedef struct {
+    double *proj_out;
+    const float *vol;
+    const float *mats;
+    int64_t nx, ny, nz, W, H;
+    double vs[3], org[3];
+    int64_t view_begin, view_end;   /* views owned by this worker */
+} adj_job;
+
+static void *adj_worker(void *arg)
+{
+    adj_job *jb = (adj_job *)arg;
+    const int64_t plane = jb->W * jb->H;
+    for (int64_t k = jb->view_begin; k < jb->view_end; ++k) {
+        double P[12];
+        for (int q = 0; q < 12; ++q) P[q] = (double)jb->mats[k * 12 + q];
+        double *img = jb->proj_out + k * plane;
+        for (int64_t z = 0; z < jb->nz; ++z) {
+            double Z = jb->org[2] + (double)z * jb->vs[2];
+            for (int64_t y = 0; y < jb->ny; ++y) {
+                double Y = jb->org[1] + (double)y * jb->vs[1];
+                const float *row = jb->vol + (z * jb->ny + y) * jb->nx;
+                for (int64_t x = 0; x < jb->nx; ++x) {
+                    double X = jb->org[0] + (double)x * jb->vs[0];
+                    int64_t i, j;
+                    double a, b, iw2;
+                    if (!oracle_cell(P, X, Y, Z, jb->W, jb->H, 0, &i, &j, &a, &b, &iw2)) continue;
+                    double g = (double)row[x] * iw2;
+                    /* transpose of the four taps: scatter g with the same weights */
+                    int64_t ms[4] = {i, i + 1, i, i + 1};
+                    int64_t ns[4] = {j, j, j + 1, j + 1};
+                    double ws[4] = {(1.0 - b) * (1.0 - a), (1.0 - b) * a, b * (1.0 - a), b * a};
+                    for (int t = 0; t < 4; ++t) {
+                        if (ms[t] < 0 || ms[t] >= jb->W || ns[t] < 0 || ns[t] >= jb->H) continue;
+                        img[ns[t] * jb->W + ms[t]] += g * ws[t];
+                    }
+                }
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Transpose of oracle_backproject: proj_out (n_views, H, W) doubles +=
+ * sum over voxels of vol * (tap weight) / w^2.  Threads split views, so each
+ * detector pixel is written by one thread in (z, y, x) voxel order. */
+int oracle_adjoint(double *proj_out, const int64_t dims[3], const double voxel_size[3],
+                   const double origin[3], const float *vol, int64_t W, int64_t H,
+                   const float *mats, int64_t n_views, int nthreads)
+{
+    if (check_geom(dims, W, H, n_views)) return -1;
+    if (n_views == 0 || dims[0] * dims[1] * dims[2] == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > ORACLE_MAX_THREADS) nthreads = ORACLE_MAX_THREADS;
+    if (nthreads > n_views) nthreads = (int)n_views;
+    adj_job *jobs = (adj_job *)calloc((size_t)nthreads, sizeof(adj_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int t = 0; t < nthreads; ++t) {
+        adj_job *jb = &jobs[t];
+        jb->proj_out = proj_out; jb->vol = vol; jb->mats = mats;
+        jb->nx = dims[0]; jb->ny = dims[1]; jb->nz = dims[2];
+        jb->W = W; jb->H = H;
+        for (int q = 0; q < 3; ++q) { jb->vs[q] = voxel_size[q]; jb->org[q] = origin[q]; }
+        jb->view_begin = n_views * t / nthreads;
+        jb->view_end = n_views * (t + 1) / nthreads;
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, adj_worker, &jobs[t]) != 0) break;
+        started = t;
+    }
+    adj_worker(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    for (int t = started + 1; t < nthreads; ++t) adj_worker(&jobs[t]);
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* Brute force for tiny cases: f(X) = sum_k sum_{m,n} I_k[n,m] tent(u-m)
+ * tent(v-n) / w^2 with tent(t) = max(0, 1-|t|), evaluated over every pixel.
+ * No floor, no cell, no bounds branches: a different route to the same
+ * bilinear, zero-extended interpolation. */
+int oracle_bruteforce(double *vol, const int64_t dims[3], const double voxel_size[3],
+                      const double origin[3], const float *proj, int64_t W, int64_t H,
+                      const float *mats, int64_t n_views)
+{
+    if (check_geom(dims, W, H, n_views)) return -1;
+    for (int64_t z = 0; z < dims[2]; ++z)
+        for (int64_t y = 0; y < dims[1]; ++y)
+            for (int64_t x = 0; x < dims[0]; ++x) {
+                double X = origin[0] + (double)x * voxel_size[0];
+                double Y = origin[1] + (double)y * voxel_size[1];
+                double Z = origin[2] + (double)z * voxel_size[2];
+                double acc = 0.0;
+                for (int64_t k = 0; k < n_views; ++k) {
+                    const float *A = mats + 12 * k;
+                    double w = A[8] * X + A[9] * Y + A[10] * Z + A[11];
+                    if (!(w > 0.0)) continue;
+                    double u = (A[0] * X + A[1] * Y + A[2] * Z + A[3]) / w;
+                    double v = (A[4] * X + A[5] * Y + A[6] * Z + A[7]) / w;
+                    double s = 0.0;
+                    for (int64_t n = 0; n < H; ++n) {
+                        double tv = 1.0 - fabs(v - (double)n);
+                        if (tv <= 0.0) continue;
+                        for (int64_t m = 0; m < W; ++m) {
+                            double tu = 1.0 - fabs(u - (double)m);
+                            if (tu <= 0.0) continue;
+                            s += (double)proj[(k * H + n) * W + m] * tu * tv;
+                        }
+                    }
+                    acc += s / (w * w);
+                }
+                vol[(z * dims[1] + y) * dims[0] + x] += acc;
+            }
+    return 0;
+}
