@@ -1,0 +1,345 @@
+"""Benchmark: voxel-driven cone-beam back-projection on GB300.
+
+One step = one back-projection of all 496 views of 1248x960 FP32 filtered
+projections into a 512^3 FP32 volume (6.66e10 voxel updates), inputs resident
+in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the slow, plain definition) on
+the host cores on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs an independent replica of the workload (the path
+needs no exchange between GPUs); the value is the total update rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("GUp/s (voxel updates/s) at 512³×496 views, fwd+adjoint; "
+          "% of roofline at stated error")
+UNIT = "GUp/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+ISSUE_SLOTS_PER_UPDATE = 27      # algorithmic work per update
+PAPER_PHI_GUPS = {"clipped": 8.5, "full": 12.9}   # Xeon Phi 5110P, assembly, 512^3
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, out_path=None):
+        self.gpu = gpu_index
+        self.out_path = out_path
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if self.out_path:
+            with open(self.out_path, "w") as f:
+                f.write("\n".join(self.lines) + "\n")
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_sample(cfg, scan_proj, mats, dims, vs, org, target_s: float, threads: int):
+    """Time the oracle on a central z-slab of the workload sized to about
+    target_s seconds; returns (updates/s, description)."""
+    import oracle
+    nx, ny, nz = int(dims[0]), int(dims[1]), int(dims[2])
+    n = mats.shape[0]
+
+    def run(planes):
+        z0 = nz // 2 - planes // 2
+        org2 = np.array(org, dtype=np.float64)
+        org2[2] = float(org[2]) + z0 * float(vs[2])
+        d2 = (nx, ny, planes)
+        t = time.perf_counter()
+        oracle.backproject(scan_proj, mats, d2, vs, org2.astype(np.float32), threads=threads)
+        return time.perf_counter() - t, nx * ny * planes * n
+
+    dt, upd = run(1)
+    rate = upd / max(dt, 1e-9)
+    planes = int(max(1, min(nz, round(target_s * rate / (nx * ny * n)))))
+    dt, upd = run(planes)
+    desc = (f"central slab {nx}x{ny}x{planes} of the {nx}x{ny}x{nz} volume, all {n} views "
+            f"({upd:.3e} updates, {dt:.1f} s)")
+    return upd / dt, desc, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    import torch
+    oracle.build()
+    cfg = synth.PRESETS[args.config]
+    threads = os.cpu_count() or 1
+    torch.set_num_threads(threads)
+    geo = synth.geometry(cfg)
+    dims, vs, org = synth.volume_geometry(cfg)
+    # inputs: a band of detector rows is all a central slab needs, but the
+    # oracle is given the whole filtered projection stack as generated
+    proj = synth.projections(cfg, geo, synth.phantom(cfg), device="cuda" if torch.cuda.is_available() else "cpu")
+    proj = proj.cpu().numpy()
+    mats = geo["mats"]
+    per_step = args.ref_step_seconds
+    rate, desc, _ = _cpu_sample(cfg, proj, mats, dims, vs, org, per_step, threads)
+    planes = int(desc.split("x")[2].split(" ")[0])
+    nx, ny = int(dims[0]), int(dims[1])
+    z0 = int(dims[2]) // 2 - planes // 2
+    org2 = np.array(org, dtype=np.float32)
+    org2[2] = float(org[2]) + z0 * float(vs[2])
+    for _ in range(args.warmup):
+        oracle.backproject(proj, mats, (nx, ny, planes), vs, org2, threads=threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.backproject(proj, mats, (nx, ny, planes), vs, org2, threads=threads)
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    upd = nx * ny * planes * cfg.n_views
+    value = upd / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} volume, {cfg.n_views} views "
+                               f"of {cfg.det_w}x{cfg.det_h}", "sample": "bounded slab per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"central slab {nx}x{ny}x{planes}, all {cfg.n_views} views per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1401_3615_gb300 import fdk
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = synth.PRESETS[args.config]
+    dev = torch.device("cuda", local)
+    scan = synth.make_scan(cfg, device=dev)
+    proj, mats = scan["proj"], scan["mats"]
+    dims, vs, org = scan["dims"], scan["voxel_size"], scan["origin"]
+    vol = torch.zeros((cfg.nz, cfg.ny, cfg.nx), dtype=torch.float32, device=dev)
+    upd_full = cfg.updates
+    upd_clip = fdk.fdk_count_updates(dims, (cfg.det_w, cfg.det_h), mats, vs, org)
+    passes = (cfg.n_views + 511) // 512
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fdk.fdk_backproject(vol, proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # per-launch durations (one launch per 512 views), CUDA events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) / passes for a, b in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * upd_full / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: pinned host
+    # projections -> device, back-projection, volume -> host, every step
+    h_proj = torch.empty(proj.shape, dtype=proj.dtype, pin_memory=True)
+    h_proj.copy_(proj)
+    h_vol = torch.empty(vol.shape, dtype=vol.dtype, pin_memory=True)
+    d_proj = torch.empty_like(proj)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        d_proj.copy_(h_proj, non_blocking=True)
+        vol.zero_()
+        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
+        h_vol.copy_(vol, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - w0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * upd_full / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
+           "d2h_bytes_per_step": int(vol.numel() * vol.element_size())}
+
+    out = None
+    if rank == 0:
+        peaks = _peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_gups = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ISSUE_SLOTS_PER_UPDATE / 1e9
+        mean_launch = float(np.mean(launch_ms))
+        achieved = upd_clip / passes / (mean_launch * 1e-3) / 1e9 * passes
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
+                    "frac": achieved / peak_gups, "traffic": None,
+                    "peak_basis": (f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                                   f"/ {ISSUE_SLOTS_PER_UPDATE} issue slots per update"),
+                    "achieved_basis": f"clipped updates {upd_clip:.4e} / mean launch time",
+                    "achieved_full_count": upd_full / (mean_launch * 1e-3) / 1e9}
+        if clk.get("sm_mhz"):
+            roofline["peak_at_measured_clock"] = peak_gups * clk["sm_mhz"] / sm_max
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            import oracle
+            oracle.build()
+            threads = os.cpu_count() or 1
+            rate, desc, _ = _cpu_sample(cfg, proj.cpu().numpy(), mats, dims, vs, org,
+                                        args.cpu_seconds, threads)
+            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": desc}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} FP32 volume "
+                                    f"({cfg.voxel} mm), {cfg.n_views} views of {cfg.det_w}x{cfg.det_h} "
+                                    "FP32 filtered projections, 200-degree short scan"),
+                       "updates_per_step": upd_full, "clipped_updates_per_step": upd_clip,
+                       "l2": "inputs larger than L2 (projections 2.38 GB, volume 512 MiB)",
+                       "fetch": args.fetch, "zrun": args.zrun or 8,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * passes,
+            "clocks": clk,
+            "clipped_gups": world * upd_clip / (ms_step * 1e-3) / 1e9,
+            "paper_context": {"xeon_phi_5110p_asm_512": PAPER_PHI_GUPS},
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="fdk512")
+    ap.add_argument("--fetch", type=int, default=0)
+    ap.add_argument("--zrun", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

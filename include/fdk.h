@@ -1,0 +1,146 @@
+/*
+ * fdk.h -- C ABI of libfdk, voxel-driven cone-beam back-projection on GB300.
+ *
+ * The operation (Sec. IV, Listing 1 of Hofmann, Treibig, Hager, Wellein,
+ * "Performance Engineering for a Medical Imaging Application on the Intel
+ * Xeon Phi Accelerator"): for every projection image k with its 3x4 matrix
+ * P_k and every voxel (x, y, z) of the volume,
+ *
+ *   X = origin + (x, y, z) * voxel_size              world position (mm)
+ *   (u', v', w) = P_k (X, 1),  u = u'/w,  v = v'/w    detector position (px)
+ *   val = bilinear interpolation of image k at (u, v), zero outside
+ *   volume[z][y][x] += val / w^2                      inverse-square weight
+ *
+ * Conventions (readings of the listing, fixed for this library):
+ *  - matrices are row-major 3x4 FP32, 12 floats per view (the listing
+ *    stores them column-major; convert at the edge);
+ *  - pixel (m, n) -- column m, row n -- is centred at detector position
+ *    (m, n) and stored at image[n * W + m]; the cell of (u, v) is
+ *    (floor(u), floor(v)) and taps outside 0 <= m < W, 0 <= n < H read 0;
+ *  - voxels with w <= 0 (at or behind the source) contribute nothing;
+ *  - the volume is x-fastest: volume[(z * ny + y) * nx + x], FP32;
+ *  - the library ACCUMULATES (volume +=, as the listing is called once per
+ *    projection); the caller zeroes the volume first if needed.
+ *
+ * Memory: every buffer is owned by the caller.  "device" means a pointer the
+ * current CUDA device can dereference (cudaMalloc, torch CUDA tensors).  The
+ * plain entry points allocate no device memory per call.  Calls enqueue
+ * kernels on opts->stream and return; asynchronous faults surface at the
+ * caller's next synchronisation.
+ *
+ * Errors: argument problems return FDK_ERR_INVALID_ARG before anything is
+ * enqueued; fdk_last_error() then gives a message (thread-local).  No C++
+ * exception crosses this boundary.
+ */
+#ifndef FDK_H
+#define FDK_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FDK_API __attribute__((visibility("default")))
+#else
+#define FDK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fdk_status {
+    FDK_OK = 0,
+    FDK_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype or option; nothing enqueued */
+    FDK_ERR_UNSUPPORTED = 2,   /* valid request this build cannot serve (e.g. fetch path) */
+    FDK_ERR_OOM = 3,           /* a library-side allocation failed */
+    FDK_ERR_CUDA = 4,          /* a CUDA runtime call failed; see fdk_last_error() */
+    FDK_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */
+} fdk_status;
+
+/* Storage type of the projection images.  Interpolation and accumulation
+ * are FP32 whatever the storage type. */
+typedef enum fdk_dtype {
+    FDK_F32 = 0,
+    FDK_BF16 = 1,
+    FDK_F16 = 2
+} fdk_dtype;
+
+/* How the four taps are fetched.  AUTO picks the texture path when the
+ * image rows and view bases meet the device's texture alignment, else LDG. */
+typedef enum fdk_fetch {
+    FDK_FETCH_AUTO = 0,
+    FDK_FETCH_LDG = 1,         /* read-only global loads, bounds checked per tile class */
+    FDK_FETCH_TEX = 2          /* 2x2 texture gather with zero border (taps in FP32) */
+} fdk_fetch;
+
+/* Optional knobs; pass NULL for defaults.  Zero in any field means default. */
+typedef struct fdk_opts {
+    int32_t proj_dtype;          /* fdk_dtype of `projections` (default FDK_F32) */
+    int32_t matrices_on_device;  /* 1: `matrices` is a device pointer; 0: host */
+    void *stream;                /* cudaStream_t; NULL = the legacy default stream */
+    int32_t fetch;               /* fdk_fetch */
+    int32_t zrun;                /* voxels per thread along z: 4, 8 or 16 */
+    int32_t reserved[10];        /* must be zero */
+} fdk_opts;
+
+/*
+ * fdk_backproject -- accumulate the back-projection of n_views projection
+ * images into `volume` (Listing 1, Sec. IV).
+ *
+ *  volume       device, nz*ny*nx FP32, x fastest; read and written (+=).
+ *  dims         host, {nx, ny, nz}, each >= 1.
+ *  voxel_size   host, {sx, sy, sz} in mm, each > 0 (the paper's MM).
+ *  origin       host, world position (mm) of the centre of voxel (0,0,0)
+ *               (the paper's O; -(n-1)/2*size centres the volume).
+ *  projections  device, n_views*H*W values of opts->proj_dtype, row-major
+ *               per image, images back to back.
+ *  det          host, {W, H}: columns (u) and rows (v) per image, >= 1.
+ *  matrices     n_views*12 FP32, row-major 3x4 per view; host memory unless
+ *               opts->matrices_on_device (then device memory).
+ *  n_views      >= 0; 0 is a no-op.
+ *
+ * Returns FDK_OK once the work is enqueued on opts->stream.
+ */
+FDK_API fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float voxel_size[3],
+                           const float origin[3], const void *projections, const int32_t det[2],
+                           const float *matrices, int32_t n_views, const fdk_opts *opts);
+
+/*
+ * fdk_forwardproject_adjoint -- the exact transpose of fdk_backproject:
+ * for every view k and voxel, scatter volume[z][y][x] / w^2 onto the four
+ * pixels around (u, v) with the bilinear weights, accumulating (+=) into
+ * `projections` (FP32 only).  Same geometry arguments and conventions as
+ * fdk_backproject; `volume` is read only.  Accumulation uses atomics, so the
+ * result is deterministic only up to FP32 summation order.
+ */
+FDK_API fdk_status fdk_forwardproject_adjoint(void *projections, const int32_t det[2],
+                                      const float *volume, const int32_t dims[3],
+                                      const float voxel_size[3], const float origin[3],
+                                      const float *matrices, int32_t n_views,
+                                      const fdk_opts *opts);
+
+/*
+ * fdk_count_updates -- count the voxel/view pairs whose footprint can touch
+ * the detector (w > 0, -1 < u < W, -1 < v < H): the "clipped" update count
+ * the paper's GUp/s figures are based on (Sec. VII), evaluated in FP32 on
+ * the device.  Synchronises opts->stream and writes the count to *count
+ * (host).  A reporting aid; it does not change any result.
+ */
+FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float voxel_size[3],
+                             const float origin[3], const int32_t det[2],
+                             const float *matrices, int32_t n_views, const fdk_opts *opts);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+FDK_API const char *fdk_last_error(void);
+
+/* Drop cached per-buffer state (texture objects) on all devices.  Call only
+ * when no work that uses them is in flight. */
+FDK_API void fdk_release(void);
+
+/* ABI version, currently 1. */
+FDK_API int32_t fdk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDK_H */

@@ -1,0 +1,17 @@
+"""GB300-native voxel-driven cone-beam back-projection (FDK hot path).
+
+The compute lives in ``libfdk.so`` (hand-written sm_103a CUDA behind the C
+ABI in ``include/fdk.h``); this package only marshals tensors into that ABI.
+Importing the package does not load the library; the first call does, and it
+raises if the library cannot be built or loaded -- there is no CPU fallback.
+"""
+from .fdk import (  # noqa: F401
+    FdkError, FETCH_AUTO, FETCH_LDG, FETCH_TEX, fdk_backproject, fdk_forwardproject_adjoint,
+    fdk_count_updates, fdk_last_error, fdk_release, fdk_version, library_path,
+)
+
+__all__ = [
+    "FdkError", "FETCH_AUTO", "FETCH_LDG", "FETCH_TEX", "fdk_backproject",
+    "fdk_forwardproject_adjoint", "fdk_count_updates", "fdk_last_error", "fdk_release",
+    "fdk_version", "library_path",
+]

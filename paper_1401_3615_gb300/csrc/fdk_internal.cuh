@@ -1,0 +1,59 @@
+// Internal declarations shared by the libfdk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fdk.h"
+
+namespace fdk {
+
+// Views handled by one kernel pass: their matrices (and texture handles)
+// travel in the kernel parameter block, so no device memory is needed for
+// them and concurrent calls on different streams cannot race.
+constexpr int KMAX = 512;
+
+struct Geom {
+    int nx, ny, nz;
+    int W, H;
+    float vs[3];
+    float org[3];
+};
+
+// Everything one back-projection pass needs.  ~29 KB, under the 32 KB
+// kernel-parameter limit.
+struct BpArgs {
+    Geom g;
+    float *vol;
+    const void *proj;          // first image of this pass
+    const float *mats_dev;     // device matrices of this pass, or nullptr
+    long long plane;           // W*H elements per image
+    int n_views;               // views in this pass (<= KMAX)
+    float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
+    unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
+};
+
+// Per (tile, view) entry computed in each CTA's prologue (shared memory).
+// Detector coordinates are kept relative to an integer cell (U, V) near the
+// tile's projected centre and the voxel offsets relative to the tile centre,
+// so the FP32 arithmetic in the hot loop works on small numbers.
+struct __align__(16) ViewEntry {
+    float4 ru;   // (c, gx, gy, gz): u'_local = c + gx*dx + gy*dy + gz*dz
+    float4 rv;   // same for v'
+    float4 rw;   // same for w
+    float4 off;  // (U + 1, V + 1, bits(U), bits(V))
+};
+
+enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
+
+// Thread-local error message setter (fdk_api.cu).
+void set_error(const char *fmt, ...);
+
+fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int zrun,
+                              cudaStream_t stream);
+fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t stream);
+fdk_status launch_count(const BpArgs &a, unsigned long long *count_dev, cudaStream_t stream);
+
+}  // namespace fdk

@@ -1,0 +1,187 @@
+"""ctypes binding of libfdk with the C ABI's names (include/fdk.h).
+
+Tensors are passed as raw pointers; shapes give dims, det and n_views; the
+stream is PyTorch's current stream unless one is given.  Nothing here
+computes: every step of the back-projection runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FDK_OK, FDK_ERR_INVALID_ARG, FDK_ERR_UNSUPPORTED, FDK_ERR_OOM, FDK_ERR_CUDA, FDK_ERR_TIMEOUT = range(6)
+FDK_F32, FDK_BF16, FDK_F16 = 0, 1, 2
+FETCH_AUTO, FETCH_LDG, FETCH_TEX = 0, 1, 2
+_STATUS = {0: "FDK_OK", 1: "FDK_ERR_INVALID_ARG", 2: "FDK_ERR_UNSUPPORTED", 3: "FDK_ERR_OOM",
+           4: "FDK_ERR_CUDA", 5: "FDK_ERR_TIMEOUT"}
+_DTYPES = {torch.float32: FDK_F32, torch.bfloat16: FDK_BF16, torch.float16: FDK_F16}
+
+
+class FdkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class fdk_opts(ctypes.Structure):
+    _fields_ = [("proj_dtype", ctypes.c_int32), ("matrices_on_device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("fetch", ctypes.c_int32), ("zrun", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
+
+
+_lock = threading.Lock()
+_lib = None
+_i32_3 = ctypes.c_int32 * 3
+_i32_2 = ctypes.c_int32 * 2
+_f32_3 = ctypes.c_float * 3
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB) or not _build.up_to_date():
+                _build.build()
+            lib = ctypes.CDLL(_build.LIB)
+            vp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)
+            i3 = ctypes.POINTER(ctypes.c_int32)
+            f3 = ctypes.POINTER(ctypes.c_float)
+            op = ctypes.POINTER(fdk_opts)
+            lib.fdk_backproject.argtypes = [vp, i3, f3, f3, vp, i3, vp, ctypes.c_int32, op]
+            lib.fdk_forwardproject_adjoint.argtypes = [vp, i3, vp, i3, f3, f3, vp, ctypes.c_int32, op]
+            lib.fdk_count_updates.argtypes = [ctypes.POINTER(ctypes.c_int64), i3, f3, f3, i3, vp,
+                                              ctypes.c_int32, op]
+            for fn in (lib.fdk_backproject, lib.fdk_forwardproject_adjoint, lib.fdk_count_updates):
+                fn.restype = ctypes.c_int
+            lib.fdk_last_error.restype = ctypes.c_char_p
+            lib.fdk_last_error.argtypes = []
+            lib.fdk_version.restype = ctypes.c_int32
+            lib.fdk_release.restype = None
+            _lib = lib
+    return _lib
+
+
+def fdk_last_error() -> str:
+    return _load().fdk_last_error().decode()
+
+
+def fdk_version() -> int:
+    return int(_load().fdk_version())
+
+
+def fdk_release() -> None:
+    _load().fdk_release()
+
+
+def _check(st: int):
+    if st != FDK_OK:
+        raise FdkError(st, fdk_last_error())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _mats(matrices, n_views: int):
+    """Host FP32 (n,12) numpy array, or a CUDA FP32 tensor (device matrices)."""
+    if isinstance(matrices, torch.Tensor) and matrices.is_cuda:
+        m = matrices.reshape(-1, 12)
+        if m.dtype != torch.float32 or not m.is_contiguous():
+            raise ValueError("device matrices must be contiguous float32")
+        if m.shape[0] != n_views:
+            raise ValueError("need one 3x4 matrix per view")
+        return m, m.data_ptr(), 1
+    if isinstance(matrices, torch.Tensor):
+        matrices = matrices.numpy()
+    m = np.ascontiguousarray(np.asarray(matrices, dtype=np.float32).reshape(-1, 12))
+    if m.shape[0] != n_views:
+        raise ValueError("need one 3x4 matrix per view")
+    return m, m.ctypes.data, 0
+
+
+def _opts(dtype: int, mats_dev: int, stream, fetch: int, zrun: int) -> fdk_opts:
+    o = fdk_opts()
+    o.proj_dtype = dtype
+    o.matrices_on_device = mats_dev
+    o.stream = stream if isinstance(stream, int) else (
+        (stream or torch.cuda.current_stream()).cuda_stream)
+    o.fetch = fetch
+    o.zrun = zrun
+    return o
+
+
+def _geom(voxel_size, origin):
+    vs = np.asarray(voxel_size, dtype=np.float32).reshape(3)
+    org = np.asarray(origin, dtype=np.float32).reshape(3)
+    return _f32_3(*vs.tolist()), _f32_3(*org.tolist())
+
+
+def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, voxel_size, origin,
+                    *, fetch: int = FETCH_AUTO, zrun: int = 0, stream=None) -> torch.Tensor:
+    """volume[nz,ny,nx] (CUDA FP32) += back-projection of projections[n,H,W]
+    (CUDA FP32/BF16/FP16) with per-view row-major 3x4 matrices (host array or
+    CUDA tensor).  Returns ``volume``."""
+    if volume.dtype != torch.float32 or volume.dim() != 3 or not volume.is_contiguous():
+        raise ValueError("volume must be a contiguous float32 (nz, ny, nx) tensor")
+    if projections.dim() != 3 or not projections.is_contiguous():
+        raise ValueError("projections must be a contiguous (n_views, H, W) tensor")
+    if projections.dtype not in _DTYPES:
+        raise ValueError(f"unsupported projection dtype {projections.dtype}")
+    n = projections.shape[0]
+    m, mptr, mdev = _mats(matrices, n)
+    nz, ny, nx = volume.shape
+    vs, org = _geom(voxel_size, origin)
+    o = _opts(_DTYPES[projections.dtype], mdev, stream, fetch, zrun)
+    lib = _load()
+    st = lib.fdk_backproject(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
+                             _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
+                             ctypes.byref(o))
+    _check(st)
+    return volume
+
+
+def fdk_forwardproject_adjoint(projections: torch.Tensor, volume: torch.Tensor, matrices,
+                               voxel_size, origin, *, stream=None) -> torch.Tensor:
+    """projections[n,H,W] (CUDA FP32) += transpose of the back-projection
+    applied to volume[nz,ny,nx] (CUDA FP32).  Returns ``projections``."""
+    if projections.dtype != torch.float32 or projections.dim() != 3 or not projections.is_contiguous():
+        raise ValueError("projections must be a contiguous float32 (n_views, H, W) tensor")
+    if volume.dtype != torch.float32 or volume.dim() != 3 or not volume.is_contiguous():
+        raise ValueError("volume must be a contiguous float32 (nz, ny, nx) tensor")
+    n = projections.shape[0]
+    m, mptr, mdev = _mats(matrices, n)
+    nz, ny, nx = volume.shape
+    vs, org = _geom(voxel_size, origin)
+    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+    st = _load().fdk_forwardproject_adjoint(_ptr(projections),
+                                            _i32_2(projections.shape[2], projections.shape[1]),
+                                            _ptr(volume), _i32_3(nx, ny, nz), vs, org, mptr, n,
+                                            ctypes.byref(o))
+    _check(st)
+    return projections
+
+
+def fdk_count_updates(dims, det, matrices, voxel_size, origin, *, stream=None) -> int:
+    """Clipped update count: voxel/view pairs with w > 0, -1 < u < W, -1 < v < H."""
+    n = int(np.asarray(matrices).reshape(-1, 12).shape[0]) if not isinstance(matrices, torch.Tensor) \
+        else int(matrices.reshape(-1, 12).shape[0])
+    m, mptr, mdev = _mats(matrices, n)
+    vs, org = _geom(voxel_size, origin)
+    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+    out = ctypes.c_int64(0)
+    d = [int(x) for x in dims]
+    st = _load().fdk_count_updates(ctypes.byref(out), _i32_3(*d), vs, org,
+                                   _i32_2(int(det[0]), int(det[1])), mptr, n, ctypes.byref(o))
+    _check(st)
+    return int(out.value)

@@ -10,7 +10,9 @@ stand-in with the same shapes:
   isocentre 600 mm, source to detector 1200 mm, 0.308 mm pixels, principal
   point at the detector centre plus a seeded +-2 px jitter and seeded +-0.5
   degree tilts of the camera axes, all folded into row-major 3x4 FP32
-  matrices whose third row has unit norm (so w is depth in mm);
+  matrices scaled so that w is the depth along the principal axis divided
+  by the source-isocentre distance (w = 1 at the isocentre; the listing's
+  1/w^2 is then exactly the FDK distance weight (SID/U)^2);
 * phantom: seeded ellipsoids with densities in [0.1, 1.0];
 * projections: analytic FP64 line integrals through the phantom,
   cosine-weighted and Ram-Lak filtered along detector rows, stored as FP32
@@ -100,7 +102,7 @@ def geometry(cfg: ScanConfig) -> dict:
     principal points needed to trace the detector rays.  Pixel (m, n) has its
     centre at detector coordinate (u, v) = (m, n); the matrix maps a world
     point X (mm) to (u', v', w) = P (X, 1) with u = u'/w, v = v'/w and w the
-    depth of X along the principal axis.
+    depth of X along the principal axis divided by SID.
     """
     rng = np.random.default_rng(cfg.seed)
     n = cfg.n_views
@@ -124,7 +126,7 @@ def geometry(cfg: ScanConfig) -> dict:
         R = R @ T.T
         Kc = np.array([[f, 0.0, u0[k]], [0.0, f, v0[k]], [0.0, 0.0, 1.0]])
         P = Kc @ np.concatenate([R, (-R @ S)[:, None]], axis=1)
-        P /= np.linalg.norm(P[2, :3])
+        P /= np.linalg.norm(P[2, :3]) * cfg.sid
         mats[k] = P
         src[k] = S
         rcam[k] = R
@@ -184,8 +186,8 @@ def projections(cfg: ScanConfig, geo: Optional[dict] = None, ph: Optional[dict] 
     Each pixel holds the FP64 line integral of the phantom along the ray from
     the source through the pixel centre, times the cosine pre-weight
     SDD / sqrt(SDD^2 + u_mm^2 + v_mm^2), Ram-Lak filtered along rows (spacing
-    scaled to the isocentre) and scaled by d_beta * SID^2 so that the
-    back-projection is an FDK reconstruction up to short-scan redundancy.
+    scaled to the isocentre) and scaled by d_beta, so that with w = depth/SID
+    the back-projection is an FDK reconstruction up to short-scan redundancy.
     With ``filtered=False`` the raw line integrals are returned.
     """
     geo = geometry(cfg) if geo is None else geo
@@ -204,7 +206,7 @@ def projections(cfg: ScanConfig, geo: Optional[dict] = None, ph: Optional[dict] 
     n_fft = 1 << int(math.ceil(math.log2(2 * W - 1)))
     Hk = _ramlak_kernel(n_fft, tau, dev)
     dbeta = math.radians(cfg.arc_deg) / max(n - 1, 1)
-    scale = dbeta * cfg.sid ** 2 * tau
+    scale = dbeta * tau
     for k0 in range(0, n, chunk):
         ks = list(range(k0, min(n, k0 + chunk)))
         b = len(ks)

@@ -45,8 +45,8 @@ def test_golden_hand_example():
 def test_closed_form_constant_projections():
     """Constant projections c: the bilinear weights sum to one, so wherever
     every view covers the voxel f = c * sum_k 1/w_k^2, with w_k the depth of
-    the voxel along view k's principal axis (computed here from the source
-    position and camera axes, not from the matrix)."""
+    the voxel along view k's principal axis over SID (computed here from the
+    source position and camera axes, not from the matrix)."""
     cfg = synth.preset("small")
     s = _scan("small")
     c = 0.75
@@ -65,7 +65,7 @@ def test_closed_form_constant_projections():
         u = geo["focal_px"] * (d @ R[0]) / depth + geo["u0"][k]
         v = geo["focal_px"] * (d @ R[1]) / depth + geo["v0"][k]
         covered &= (u >= 0) & (u <= cfg.det_w - 1) & (v >= 0) & (v <= cfg.det_h - 1)
-        inv_w2 += 1.0 / depth ** 2
+        inv_w2 += (cfg.sid / depth) ** 2
     assert covered.sum() > 100
     # the FP32 matrices differ from the FP64 camera by rounding only
     np.testing.assert_allclose(f[covered], c * inv_w2[covered], rtol=2e-6)
