@@ -182,6 +182,43 @@ def run_reference(args):
     return 0
 
 
+def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
+    """End to end through the public API with host buffers: every step copies
+    the projections from pinned host memory to the device, back-projects
+    into a zeroed volume and reads the volume back to pinned host memory."""
+    import torch
+    import torch.distributed as dist
+    from paper_1401_3615_gb300 import fdk
+    h_proj = torch.empty(proj.shape, dtype=proj.dtype, pin_memory=True)
+    h_proj.copy_(proj)
+    h_vol = torch.empty(vol.shape, dtype=vol.dtype, pin_memory=True)
+    d_proj = torch.empty_like(proj)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        d_proj.copy_(h_proj, non_blocking=True)
+        vol.zero_()
+        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
+        h_vol.copy_(vol, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - w0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    return {"value": world * upd_full / e2e_s / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
+            "d2h_bytes_per_step": int(vol.numel() * vol.element_size())}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -196,6 +233,8 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg = synth.PRESETS[args.config]
+    if args.views:
+        cfg = synth.preset(args.config, n_views=args.views)
     dev = torch.device("cuda", local)
     scan = synth.make_scan(cfg, device=dev)
     proj, mats = scan["proj"], scan["mats"]
@@ -243,36 +282,9 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = world * upd_full / (ms_step * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers: pinned host
-    # projections -> device, back-projection, volume -> host, every step
-    h_proj = torch.empty(proj.shape, dtype=proj.dtype, pin_memory=True)
-    h_proj.copy_(proj)
-    h_vol = torch.empty(vol.shape, dtype=vol.dtype, pin_memory=True)
-    d_proj = torch.empty_like(proj)
-    e2e_steps = max(1, min(args.steps, 5))
-
-    def e2e_step():
-        d_proj.copy_(h_proj, non_blocking=True)
-        vol.zero_()
-        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
-        h_vol.copy_(vol, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    w0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - w0) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * upd_full / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
-           "d2h_bytes_per_step": int(vol.numel() * vol.element_size())}
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full)
 
     out = None
     if rank == 0:
@@ -280,7 +292,7 @@ def run_ours(args):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak_gups = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ISSUE_SLOTS_PER_UPDATE / 1e9
         mean_launch = float(np.mean(launch_ms))
-        achieved = upd_clip / passes / (mean_launch * 1e-3) / 1e9 * passes
+        achieved = upd_clip / passes / (mean_launch * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
                     "frac": achieved / peak_gups, "traffic": None,
                     "peak_basis": (f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
@@ -306,7 +318,8 @@ def run_ours(args):
                                     f"({cfg.voxel} mm), {cfg.n_views} views of {cfg.det_w}x{cfg.det_h} "
                                     "FP32 filtered projections, 200-degree short scan"),
                        "updates_per_step": upd_full, "clipped_updates_per_step": upd_clip,
-                       "l2": "inputs larger than L2 (projections 2.38 GB, volume 512 MiB)",
+                       "l2": (f"inputs larger than L2 (projections {proj.numel() * proj.element_size() / 1e9:.2f} GB, "
+                              f"volume {vol.numel() * 4 / 2**20:.0f} MiB)"),
                        "fetch": args.fetch, "zrun": args.zrun or 8,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
@@ -335,6 +348,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -64,12 +64,13 @@ typedef enum fdk_dtype {
     FDK_F16 = 2
 } fdk_dtype;
 
-/* How the four taps are fetched.  AUTO picks the texture path when the
- * image rows and view bases meet the device's texture alignment, else LDG. */
+/* How the four taps are fetched.  AUTO picks the fastest path measured on
+ * GB300, currently LDG. */
 typedef enum fdk_fetch {
     FDK_FETCH_AUTO = 0,
     FDK_FETCH_LDG = 1,         /* read-only global loads, bounds checked per tile class */
-    FDK_FETCH_TEX = 2          /* 2x2 texture gather with zero border (taps in FP32) */
+    FDK_FETCH_TEX = 2          /* 2x2 texture gather with zero border (taps in FP32); the
+                                  images are first copied into cached CUDA arrays */
 } fdk_fetch;
 
 /* Optional knobs; pass NULL for defaults.  Zero in any field means default. */

@@ -4,6 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <memory>
+#include <mutex>
+#include <vector>
+
 #include "fdk_internal.cuh"
 
 namespace fdk {
@@ -108,7 +112,118 @@ static fdk_status check_alignment(const void *p, size_t align, const char *what)
     return FDK_OK;
 }
 
-static int pick_fetch(const fdk_opts *o) { return o->fetch == FDK_FETCH_TEX ? 2 : 1; }
+// ---------------------------------------------------------------------------
+// Texture staging.  Texture gather (tld4) is defined for CUDA arrays created
+// with cudaArrayTextureGather, so the texture fetch path copies each view into
+// a 2D array (block-linear layout, zero border from the sampler) before the
+// kernel -- the GPU form of the paper's zero-padding copy (Sec. VI).  The
+// arrays are cached per (device, W, H, dtype) and reused by later calls; an
+// event recorded after each call's kernels makes the next call, on whatever
+// stream, wait before it overwrites them.
+struct TexStage {
+    int dev, W, H, dtype;
+    std::vector<cudaArray_t> arrays;
+    std::vector<cudaTextureObject_t> texs;
+    cudaEvent_t done = nullptr;
+};
+
+static std::mutex g_tex_mu;
+static std::vector<std::unique_ptr<TexStage>> g_tex;
+
+static cudaChannelFormatDesc tex_channel(int dtype)
+{
+    if (dtype == FDK_F32) return cudaCreateChannelDesc<float>();
+    if (dtype == FDK_F16) return cudaCreateChannelDescHalf();
+    return cudaCreateChannelDesc<unsigned short>();  // BF16 bits, widened in the kernel
+}
+
+static void tex_stage_free(TexStage *t)
+{
+    for (auto o : t->texs) cudaDestroyTextureObject(o);
+    for (auto a : t->arrays) cudaFreeArray(a);
+    if (t->done) cudaEventDestroy(t->done);
+    t->texs.clear();
+    t->arrays.clear();
+    t->done = nullptr;
+}
+
+// Whether this device can gather from W x H arrays at all.
+static bool tex_supported(int dev, int W, int H)
+{
+    int mw = 0, mh = 0;
+    if (cudaDeviceGetAttribute(&mw, cudaDevAttrMaxTexture2DGatherWidth, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&mh, cudaDevAttrMaxTexture2DGatherHeight, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return W <= mw && H <= mh;
+}
+
+// Find or grow the staging set for (dev, W, H, dtype) to n arrays.  Caller
+// holds g_tex_mu.  On failure everything allocated here is released.
+static fdk_status tex_stage_get(int dev, int W, int H, int dtype, int n, TexStage **out)
+{
+    TexStage *t = nullptr;
+    for (auto &p : g_tex)
+        if (p->dev == dev && p->W == W && p->H == H && p->dtype == dtype) t = p.get();
+    if (!t) {
+        g_tex.emplace_back(new TexStage());
+        t = g_tex.back().get();
+        t->dev = dev; t->W = W; t->H = H; t->dtype = dtype;
+    }
+    if (!t->done && cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "cudaEventCreate failed");
+    }
+    const cudaChannelFormatDesc ch = tex_channel(dtype);
+    while ((int)t->arrays.size() < n) {
+        cudaArray_t arr = nullptr;
+        cudaError_t e = cudaMallocArray(&arr, &ch, W, H, cudaArrayTextureGather);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("texture staging: cudaMallocArray failed: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? FDK_ERR_OOM : FDK_ERR_CUDA;
+        }
+        cudaResourceDesc rd;
+        memset(&rd, 0, sizeof rd);
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td;
+        memset(&td, 0, sizeof td);
+        td.addressMode[0] = cudaAddressModeBorder;   // zero outside the image
+        td.addressMode[1] = cudaAddressModeBorder;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        cudaTextureObject_t tex = 0;
+        e = cudaCreateTextureObject(&tex, &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeArray(arr);
+            set_error("texture staging: cudaCreateTextureObject failed: %s", cudaGetErrorString(e));
+            return FDK_ERR_CUDA;
+        }
+        t->arrays.push_back(arr);
+        t->texs.push_back(tex);
+    }
+    *out = t;
+    return FDK_OK;
+}
+
+void release_textures()
+{
+    std::lock_guard<std::mutex> lk(g_tex_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &p : g_tex) {
+        cudaSetDevice(p->dev);
+        cudaDeviceSynchronize();
+        tex_stage_free(p.get());
+    }
+    g_tex.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
 
 }  // namespace fdk
 
@@ -120,7 +235,7 @@ const char *fdk_last_error(void) { return g_err; }
 
 int32_t fdk_version(void) { return 1; }
 
-void fdk_release(void) {}
+void fdk_release(void) { release_textures(); }
 
 fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float voxel_size[3],
                            const float origin[3], const void *projections, const int32_t det[2],
@@ -143,11 +258,38 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     if ((st = check_device_ptr(volume, "volume"))) return st;
     if ((st = check_device_ptr(projections, "projections"))) return st;
     if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
-    if (o->fetch == FDK_FETCH_TEX) return fail(FDK_ERR_UNSUPPORTED, "texture fetch path not built");
-    const int fetch = pick_fetch(o);
     cudaStream_t s = (cudaStream_t)o->stream;
     const size_t esz = dtype_size(o->proj_dtype);
     const long long plane = (long long)g.W * g.H;
+    int dev = 0;
+    cudaGetDevice(&dev);
+
+    // texture path only on request: on GB300 the 2x2 gather rate of the
+    // texture units is below what the LDG path reaches
+    bool use_tex = false;
+    TexStage *stage = nullptr;
+    std::unique_lock<std::mutex> lk(g_tex_mu, std::defer_lock);
+    if (o->fetch == FDK_FETCH_TEX) {
+        if (!tex_supported(dev, g.W, g.H)) {
+            if (o->fetch == FDK_FETCH_TEX)
+                return fail(FDK_ERR_UNSUPPORTED, "detector exceeds the device's texture-gather size");
+        } else {
+            lk.lock();
+            st = tex_stage_get(dev, g.W, g.H, o->proj_dtype, n_views < KMAX ? n_views : KMAX, &stage);
+            if (st == FDK_OK) {
+                use_tex = true;
+            } else if (o->fetch == FDK_FETCH_TEX) {
+                return st;
+            } else {
+                lk.unlock();
+                g_err[0] = 0;   // AUTO: fall back to the LDG path
+            }
+        }
+    }
+    if (use_tex && cudaStreamWaitEvent(s, stage->done, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "cudaStreamWaitEvent failed");
+    }
 
     for (int v0 = 0; v0 < n_views; v0 += KMAX) {
         const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
@@ -162,8 +304,23 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
             a.mats_dev = nullptr;
             memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
         }
-        if ((st = launch_backproject(a, fetch, o->proj_dtype, o->zrun ? o->zrun : 8, s))) return st;
+        if (use_tex) {
+            for (int k = 0; k < nv; ++k) {
+                const char *src = static_cast<const char *>(a.proj) + (size_t)k * plane * esz;
+                cudaError_t e = cudaMemcpy2DToArrayAsync(stage->arrays[k], 0, 0, src, g.W * esz,
+                                                         g.W * esz, g.H, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    set_error("texture staging copy failed: %s", cudaGetErrorString(e));
+                    return FDK_ERR_CUDA;
+                }
+                a.tex[k] = (unsigned long long)stage->texs[k];
+            }
+        }
+        if ((st = launch_backproject(a, use_tex ? 2 : 1, o->proj_dtype, o->zrun ? o->zrun : 8, s)))
+            return st;
     }
+    if (use_tex) cudaEventRecord(stage->done, s);
     return FDK_OK;
 }
 

@@ -8,12 +8,15 @@
 // order as the definition.
 //
 // Per view and voxel the hot loop does, in FP32:
-//   u'_l, v'_l, w   = three FMAs from per-(tile, view) coefficients
-//   r = 1/w (MUFU), u = u'_l r, v = v'_l r (cell-relative detector position)
-//   floor, fractions a, b
-//   four taps: a 2x2 texture gather with zero border (TEX path), or four
-//   read-only loads (LDG path, bounds-checked only on boundary tiles)
-//   three lerps, acc += val * r * r
+//   (u'_l, v'_l), w = FMAs from per-(tile, view) coefficients
+//   r = 1/w (MUFU), (u, v) = (u'_l, v'_l) r, cell-relative detector position
+//   floor and fractions (a, b) by a round-down magic add
+//   four taps: read-only loads (LDG path: bounds-free on interior tiles) or
+//   a 2x2 texture gather with zero border (TEX path)
+//   three lerps, acc += val r^2
+// The u/v pair of one voxel and the w, weight and accumulator of two z
+// neighbours are processed as packed f32x2 operations (FFMA2/FADD2/FMUL2),
+// which halves the issue slots of the FP32 work.
 #include "fdk_tile.cuh"
 
 namespace fdk {
@@ -36,7 +39,7 @@ template <> struct Elem<__nv_bfloat16> {
 // 2x2 gather of texels (i, j), (i+1, j), (i, j+1), (i+1, j+1) returned as
 // (p00, p10, p01, p11).  (x, y) = (i + 1, j + 1) sits exactly on the corner
 // shared by the four texel centres, so the hardware footprint selection
-// agrees with floor() in FP32.
+// agrees with the FP32 floor.
 template <typename T> struct Gather;
 template <> struct Gather<float> {
     static __device__ __forceinline__ float4 fetch(cudaTextureObject_t t, float x, float y)
@@ -63,63 +66,121 @@ template <> struct Gather<__nv_bfloat16> {
 
 enum Fetch : int { kLdg = 1, kTex = 2 };
 
-// One view against this thread's R voxels.  MODE: kInterior (no checks),
-// kBoundary (tap bounds checks), kGeneral (bounds and per-voxel w > 0).
-template <int R, int FETCH, int MODE, typename T>
-__device__ __forceinline__ void bp_view(float (&acc)[R], const ViewEntry &e, float dxf, float dyf,
-                                        const T *img, int W, int H, cudaTextureObject_t tex)
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// Bilinear value from the four taps and the fractions (a, b):
+// lo = p00 + a (p10 - p00), hi = p01 + a (p11 - p01), val = lo + b (hi - lo).
+__device__ __forceinline__ float bilerp(float p00, float p10, float p01, float p11, float2 ab)
 {
-    const float bu = fmaf(dyf, e.ru.z, fmaf(dxf, e.ru.y, e.ru.x));
-    const float bv = fmaf(dyf, e.rv.z, fmaf(dxf, e.rv.y, e.rv.x));
-    const float bw = fmaf(dyf, e.rw.z, fmaf(dxf, e.rw.y, e.rw.x));
-    const int U = __float_as_int(e.off.z), V = __float_as_int(e.off.w);
+    const float2 d = __ffma2_rn(f2(p00, p01), f2(-1.0f), f2(p10, p11));
+    const float2 lh = __ffma2_rn(f2(ab.x), d, f2(p00, p01));
+    return fmaf(ab.y, lh.y - lh.x, lh.x);
+}
+
+// Per-thread values of one view: (u'_l, v'_l) and w at z offset 0.
+struct ViewBase {
+    float2 uv;
+    float w;
+};
+
+__device__ __forceinline__ ViewBase view_base(const ViewEntry &e, float dxf, float dyf)
+{
+    ViewBase b;
+    b.uv = __ffma2_rn(f2(dyf), f2(e.b.x, e.b.y), __ffma2_rn(f2(dxf), f2(e.a.z, e.a.w), f2(e.a.x, e.a.y)));
+    b.w = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
+    return b;
+}
+
+// Interior tiles: all four taps of every voxel lie inside the image.
+// FIDX: the flat tap index is formed in FP32 (exact while W*H < 2^23) and its
+// bit pattern used as the address offset; otherwise integer arithmetic.
+template <int R, typename T, bool FIDX>
+__device__ __forceinline__ void view_interior_ldg(float (&acc)[R], const ViewEntry &e, float dxf,
+                                                  float dyf, const T *img, int W)
+{
+    const ViewBase vb = view_base(e, dxf, dyf);
+    const float2 gz = f2(e.b.z, e.b.w);
+    const float2 M = f2(kFloorMagic);
+    const float Wf = (float)W;
+    const int U = (int)e.o.x, V = (int)e.o.y;
+    // row pointers biased so the index bits address the tap directly
+    const unsigned long long row0 =
+        FIDX ? (unsigned long long)img - (unsigned long long)kIndexBits * sizeof(T)
+             : (unsigned long long)img;
+    const unsigned long long row1 = row0 + (unsigned long long)W * sizeof(T);
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+        const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
+        const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(vb.w));
+        const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
+        const float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, vb.uv), f2(iw0));
+        const float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, vb.uv), f2(iw1));
+        const float2 t0 = __fadd2_rd(uv0, M), t1 = __fadd2_rd(uv1, M);
+        const float2 fl0 = __fadd2_rn(t0, f2(-kFloorMagic)), fl1 = __fadd2_rn(t1, f2(-kFloorMagic));
+        const float2 ab0 = __ffma2_rn(fl0, f2(-1.0f), uv0), ab1 = __ffma2_rn(fl1, f2(-1.0f), uv1);
+        unsigned long long o0, o1;
+        if (FIDX) {
+            const float2 s = __ffma2_rn(f2(fl0.y, fl1.y), f2(Wf), f2(fl0.x, fl1.x));
+            const float2 k = __fadd2_rn(s, f2(e.o.z));
+            o0 = (unsigned long long)__float_as_uint(k.x) * sizeof(T);
+            o1 = (unsigned long long)__float_as_uint(k.y) * sizeof(T);
+        } else {
+            const int i0 = __float_as_int(t0.x) - kFloorBits + U, j0 = __float_as_int(t0.y) - kFloorBits + V;
+            const int i1 = __float_as_int(t1.x) - kFloorBits + U, j1 = __float_as_int(t1.y) - kFloorBits + V;
+            o0 = (unsigned long long)(j0 * W + i0) * sizeof(T);
+            o1 = (unsigned long long)(j1 * W + i1) * sizeof(T);
+        }
+        const T *q00 = reinterpret_cast<const T *>(row0 + o0);
+        const T *q01 = reinterpret_cast<const T *>(row1 + o0);
+        const T *q10 = reinterpret_cast<const T *>(row0 + o1);
+        const T *q11 = reinterpret_cast<const T *>(row1 + o1);
+        const float v0 = bilerp(Elem<T>::load(q00), Elem<T>::load(q00 + 1), Elem<T>::load(q01),
+                                Elem<T>::load(q01 + 1), ab0);
+        const float v1 = bilerp(Elem<T>::load(q10), Elem<T>::load(q10 + 1), Elem<T>::load(q11),
+                                Elem<T>::load(q11 + 1), ab1);
+        const float2 w2 = __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1));
+        const float2 s2 = __ffma2_rn(f2(v0, v1), w2, f2(acc[r], acc[r + 1]));
+        acc[r] = s2.x;
+        acc[r + 1] = s2.y;
+    }
+}
+
+// Boundary (and, with GENERAL, source-plane-crossing) tiles on the LDG path:
+// per-tap bounds checks, loads only for taps inside the image.
+template <int R, typename T, bool GENERAL>
+__device__ __forceinline__ void view_checked_ldg(float (&acc)[R], const ViewEntry &e, float dxf,
+                                                 float dyf, const T *img, int W, int H)
+{
+    const ViewBase vb = view_base(e, dxf, dyf);
+    const float2 gz = f2(e.b.z, e.b.w);
+    const int U = (int)e.o.x, V = (int)e.o.y;
+    // cell-relative clamp range keeping every int exact; taps there read 0
+    const float2 lo = f2(-2.0f - e.o.x, -2.0f - e.o.y);
+    const float2 hi = f2((float)(W + 1) - e.o.x, (float)(H + 1) - e.o.y);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float rf = (float)(r - R / 2);
-        const float ul = fmaf(rf, e.ru.w, bu);
-        const float vl = fmaf(rf, e.rv.w, bv);
-        const float wl = fmaf(rf, e.rw.w, bw);
+        const float wl = fmaf(rf, e.w.w, vb.w);
         const float iw = rcp_approx(wl);
-        float us = ul * iw, vs = vl * iw;
-        if (MODE != kInterior) {
-            // keep far-off rays in a range where the int conversions are exact;
-            // every tap there is outside the image either way
-            us = fminf(fmaxf(us, -4.0f - (float)U), (float)(W + 4 - U));
-            vs = fminf(fmaxf(vs, -4.0f - (float)V), (float)(H + 4 - V));
-        }
-        const float fu = floorf(us), fv = floorf(vs);
-        const float a = us - fu, b = vs - fv;
-        float p00, p10, p01, p11;
-        if (FETCH == kTex) {
-            const float4 g = Gather<T>::fetch(tex, fu + e.off.x, fv + e.off.y);
-            p00 = g.x; p10 = g.y; p01 = g.z; p11 = g.w;
-        } else if (MODE == kInterior) {
-            const T *p = img + ((int)fv + V) * W + ((int)fu + U);
-            p00 = Elem<T>::load(p);
-            p10 = Elem<T>::load(p + 1);
-            p01 = Elem<T>::load(p + W);
-            p11 = Elem<T>::load(p + W + 1);
-        } else {
-            const int i = (int)fu + U, j = (int)fv + V;
-            const bool c0 = (unsigned)i < (unsigned)W, c1 = (unsigned)(i + 1) < (unsigned)W;
-            const bool r0 = (unsigned)j < (unsigned)H, r1 = (unsigned)(j + 1) < (unsigned)H;
-            // clamp the address into the image, zero the tap if it was outside
-            const int ic0 = min(max(i, 0), W - 1), ic1 = min(max(i + 1, 0), W - 1);
-            const int jc0 = min(max(j, 0), H - 1), jc1 = min(max(j + 1, 0), H - 1);
-            p00 = Elem<T>::load(img + jc0 * W + ic0);
-            p10 = Elem<T>::load(img + jc0 * W + ic1);
-            p01 = Elem<T>::load(img + jc1 * W + ic0);
-            p11 = Elem<T>::load(img + jc1 * W + ic1);
-            p00 = (c0 && r0) ? p00 : 0.0f;
-            p10 = (c1 && r0) ? p10 : 0.0f;
-            p01 = (c0 && r1) ? p01 : 0.0f;
-            p11 = (c1 && r1) ? p11 : 0.0f;
-        }
-        const float lo = fmaf(a, p10 - p00, p00);
-        const float hi = fmaf(a, p11 - p01, p01);
-        float val = fmaf(b, hi - lo, lo);
+        float2 uv = __fmul2_rn(__ffma2_rn(f2(rf), gz, vb.uv), f2(iw));
+        uv = f2(fminf(fmaxf(uv.x, lo.x), hi.x), fminf(fmaxf(uv.y, lo.y), hi.y));
+        const float2 t = __fadd2_rd(uv, f2(kFloorMagic));
+        const float2 fl = __fadd2_rn(t, f2(-kFloorMagic));
+        const float2 ab = __ffma2_rn(fl, f2(-1.0f), uv);
+        const int i = __float_as_int(t.x) - kFloorBits + U;
+        const int j = __float_as_int(t.y) - kFloorBits + V;
+        const bool c0 = (unsigned)i < (unsigned)W, c1 = (unsigned)(i + 1) < (unsigned)W;
+        const bool r0 = (unsigned)j < (unsigned)H, r1 = (unsigned)(j + 1) < (unsigned)H;
+        const T *q = img + (j * W + i);
+        float p00 = 0.0f, p10 = 0.0f, p01 = 0.0f, p11 = 0.0f;
+        if (c0 && r0) p00 = Elem<T>::load(q);
+        if (c1 && r0) p10 = Elem<T>::load(q + 1);
+        if (c0 && r1) p01 = Elem<T>::load(q + W);
+        if (c1 && r1) p11 = Elem<T>::load(q + W + 1);
+        float val = bilerp(p00, p10, p01, p11, ab);
         float iw2 = iw * iw;
-        if (MODE == kGeneral) {
+        if (GENERAL) {
             const bool front = wl > 0.0f;
             val = front ? val : 0.0f;
             iw2 = front ? iw2 : 0.0f;
@@ -128,12 +189,57 @@ __device__ __forceinline__ void bp_view(float (&acc)[R], const ViewEntry &e, flo
     }
 }
 
+// Texture path: the gather's zero border covers every off-image tap, so one
+// code path serves interior and boundary tiles.
+template <int R, typename T, bool GENERAL>
+__device__ __forceinline__ void view_tex(float (&acc)[R], const ViewEntry &e, float dxf, float dyf,
+                                         cudaTextureObject_t tex, int W, int H)
+{
+    const ViewBase vb = view_base(e, dxf, dyf);
+    const float2 gz = f2(e.b.z, e.b.w);
+    const float2 cell = f2(e.o.x + 1.0f, e.o.y + 1.0f);
+    const float2 lo = f2(-4.0f - e.o.x, -4.0f - e.o.y);
+    const float2 hi = f2((float)(W + 4) - e.o.x, (float)(H + 4) - e.o.y);
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+        const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
+        const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(vb.w));
+        const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
+        float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, vb.uv), f2(iw0));
+        float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, vb.uv), f2(iw1));
+        if (GENERAL) {
+            // keep texel coordinates finite behind the source plane
+            uv0 = f2(fminf(fmaxf(uv0.x, lo.x), hi.x), fminf(fmaxf(uv0.y, lo.y), hi.y));
+            uv1 = f2(fminf(fmaxf(uv1.x, lo.x), hi.x), fminf(fmaxf(uv1.y, lo.y), hi.y));
+        }
+        const float2 fl0 = __fadd2_rn(__fadd2_rd(uv0, f2(kFloorMagic)), f2(-kFloorMagic));
+        const float2 fl1 = __fadd2_rn(__fadd2_rd(uv1, f2(kFloorMagic)), f2(-kFloorMagic));
+        const float2 ab0 = __ffma2_rn(fl0, f2(-1.0f), uv0), ab1 = __ffma2_rn(fl1, f2(-1.0f), uv1);
+        const float2 x0 = __fadd2_rn(fl0, cell), x1 = __fadd2_rn(fl1, cell);
+        const float4 g0 = Gather<T>::fetch(tex, x0.x, x0.y);
+        const float4 g1 = Gather<T>::fetch(tex, x1.x, x1.y);
+        float v0 = bilerp(g0.x, g0.y, g0.z, g0.w, ab0);
+        float v1 = bilerp(g1.x, g1.y, g1.z, g1.w, ab1);
+        float2 w2 = __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1));
+        if (GENERAL) {
+            const bool f0 = wl.x > 0.0f, f1 = wl.y > 0.0f;
+            v0 = f0 ? v0 : 0.0f;
+            v1 = f1 ? v1 : 0.0f;
+            w2 = f2(f0 ? w2.x : 0.0f, f1 ? w2.y : 0.0f);
+        }
+        const float2 s2 = __ffma2_rn(f2(v0, v1), w2, f2(acc[r], acc[r + 1]));
+        acc[r] = s2.x;
+        acc[r + 1] = s2.y;
+    }
+}
+
 // CTA tile BX x BY x R; warps cover WX x (32/WX) voxel patches in (x, y).
-template <int BX, int BY, int WX, int R, int FETCH, typename T>
-__global__ void __launch_bounds__(BX * BY)
+template <int BX, int BY, int WX, int R, int MINB, int FETCH, typename T, bool FIDX>
+__global__ void __launch_bounds__(BX * BY, MINB)
 fdk_bp_kernel(const __grid_constant__ BpArgs a)
 {
     static_assert(32 % WX == 0 && BX % WX == 0 && BY % (32 / WX) == 0, "warp tiling");
+    static_assert(R % 2 == 0, "z-run must be even (voxel pairs)");
     constexpr int WY = 32 / WX;
     constexpr int WPX = BX / WX;
     __shared__ ViewEntry tab[KMAX];
@@ -160,14 +266,15 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
         const int ev = act[q];
         const int v = ev & 1023, c = ev >> 10;
         const ViewEntry e = tab[v];
-        const T *img = proj + (long long)v * a.plane;
-        const cudaTextureObject_t tex = (FETCH == kTex) ? (cudaTextureObject_t)a.tex[v] : 0;
-        if (c == kInterior) {
-            bp_view<R, FETCH, kInterior, T>(acc, e, dxf, dyf, img, W, H, tex);
-        } else if (c == kBoundary) {
-            bp_view<R, FETCH, kBoundary, T>(acc, e, dxf, dyf, img, W, H, tex);
+        if (FETCH == kTex) {
+            const cudaTextureObject_t tex = (cudaTextureObject_t)a.tex[v];
+            if (c != kGeneral) view_tex<R, T, false>(acc, e, dxf, dyf, tex, W, H);
+            else view_tex<R, T, true>(acc, e, dxf, dyf, tex, W, H);
         } else {
-            bp_view<R, FETCH, kGeneral, T>(acc, e, dxf, dyf, img, W, H, tex);
+            const T *img = proj + (long long)v * a.plane;
+            if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
+            else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
+            else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
         }
     }
 
@@ -183,11 +290,11 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
     }
 }
 
-template <int BX, int BY, int WX, int R, int FETCH, typename T>
+template <int BX, int BY, int WX, int R, int MINB, int FETCH, typename T, bool FIDX>
 static fdk_status launch_one(const BpArgs &a, cudaStream_t s)
 {
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + R - 1) / R);
-    fdk_bp_kernel<BX, BY, WX, R, FETCH, T><<<grid, BX * BY, 0, s>>>(a);
+    fdk_bp_kernel<BX, BY, WX, R, MINB, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error("back-projection launch failed: %s", cudaGetErrorString(err));
@@ -196,29 +303,38 @@ static fdk_status launch_one(const BpArgs &a, cudaStream_t s)
     return FDK_OK;
 }
 
-template <int FETCH, typename T>
+template <int FETCH, typename T, bool FIDX>
 static fdk_status launch_zrun(const BpArgs &a, int zrun, cudaStream_t s)
 {
     switch (zrun) {
-    case 4: return launch_one<32, 8, 8, 4, FETCH, T>(a, s);
-    case 16: return launch_one<32, 8, 8, 16, FETCH, T>(a, s);
-    default: return launch_one<32, 8, 8, 8, FETCH, T>(a, s);
+    case 4: return launch_one<32, 8, 8, 4, 4, FETCH, T, FIDX>(a, s);
+    case 16: return launch_one<32, 8, 8, 16, 3, FETCH, T, FIDX>(a, s);
+    default: return launch_one<32, 8, 8, 8, 4, FETCH, T, FIDX>(a, s);
     }
+}
+
+template <int FETCH, typename T>
+static fdk_status launch_typed(const BpArgs &a, int zrun, cudaStream_t s)
+{
+    // the float flat index is exact while every tap index is below 2^23
+    const bool fidx = (long long)a.g.W * (a.g.H + 1) < (1LL << 23);
+    if (FETCH == kLdg && fidx) return launch_zrun<FETCH, T, true>(a, zrun, s);
+    return launch_zrun<FETCH, T, false>(a, zrun, s);
 }
 
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int zrun, cudaStream_t s)
 {
     if (fetch == kTex) {
         switch (dtype) {
-        case FDK_F32: return launch_zrun<kTex, float>(a, zrun, s);
-        case FDK_F16: return launch_zrun<kTex, __half>(a, zrun, s);
-        case FDK_BF16: return launch_zrun<kTex, __nv_bfloat16>(a, zrun, s);
+        case FDK_F32: return launch_typed<kTex, float>(a, zrun, s);
+        case FDK_F16: return launch_typed<kTex, __half>(a, zrun, s);
+        case FDK_BF16: return launch_typed<kTex, __nv_bfloat16>(a, zrun, s);
         }
     } else {
         switch (dtype) {
-        case FDK_F32: return launch_zrun<kLdg, float>(a, zrun, s);
-        case FDK_F16: return launch_zrun<kLdg, __half>(a, zrun, s);
-        case FDK_BF16: return launch_zrun<kLdg, __nv_bfloat16>(a, zrun, s);
+        case FDK_F32: return launch_typed<kLdg, float>(a, zrun, s);
+        case FDK_F16: return launch_typed<kLdg, __half>(a, zrun, s);
+        case FDK_BF16: return launch_typed<kLdg, __nv_bfloat16>(a, zrun, s);
         }
     }
     set_error("unsupported projection dtype %d", dtype);

@@ -23,17 +23,16 @@ fdk_count_kernel(const __grid_constant__ BpArgs a, unsigned long long *count)
     if (x < a.g.nx && y < a.g.ny) {
         for (int q = 0; q < n_act; ++q) {
             const ViewEntry e = tab[act[q] & 1023];
-            const int U = __float_as_int(e.off.z), V = __float_as_int(e.off.w);
-            const float bu = fmaf(dyf, e.ru.z, fmaf(dxf, e.ru.y, e.ru.x));
-            const float bv = fmaf(dyf, e.rv.z, fmaf(dxf, e.rv.y, e.rv.x));
-            const float bw = fmaf(dyf, e.rw.z, fmaf(dxf, e.rw.y, e.rw.x));
+            const float bu = fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x));
+            const float bv = fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y));
+            const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
             for (int r = 0; r < R && z0 + r < a.g.nz; ++r) {
                 const float rf = (float)(r - R / 2);
-                const float wl = fmaf(rf, e.rw.w, bw);
+                const float wl = fmaf(rf, e.w.w, bw);
                 if (!(wl > 0.0f)) continue;
                 const float iw = rcp_approx(wl);
-                const float u = fmaf(rf, e.ru.w, bu) * iw + (float)U;
-                const float v = fmaf(rf, e.rv.w, bv) * iw + (float)V;
+                const float u = fmaf(fmaf(rf, e.b.z, bu), iw, e.o.x);
+                const float v = fmaf(fmaf(rf, e.b.w, bv), iw, e.o.y);
                 c += (u > -1.0f && u < (float)a.g.W && v > -1.0f && v < (float)a.g.H) ? 1 : 0;
             }
         }

@@ -38,12 +38,13 @@ struct BpArgs {
 // Per (tile, view) entry computed in each CTA's prologue (shared memory).
 // Detector coordinates are kept relative to an integer cell (U, V) near the
 // tile's projected centre and the voxel offsets relative to the tile centre,
-// so the FP32 arithmetic in the hot loop works on small numbers.
+// so the FP32 arithmetic in the hot loop works on small numbers.  u and v
+// coefficients are interleaved so the hot loop can use packed f32x2 math.
 struct __align__(16) ViewEntry {
-    float4 ru;   // (c, gx, gy, gz): u'_local = c + gx*dx + gy*dy + gz*dz
-    float4 rv;   // same for v'
-    float4 rw;   // same for w
-    float4 off;  // (U + 1, V + 1, bits(U), bits(V))
+    float4 a;    // (c_u, c_v, gx_u, gx_v): value at the tile centre, step in x
+    float4 b;    // (gy_u, gy_v, gz_u, gz_v): steps in y and z
+    float4 w;    // (c_w, gx_w, gy_w, gz_w)
+    float4 o;    // (U, V, V*W + U + 2^23, 0)
 };
 
 enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
@@ -53,6 +54,7 @@ void set_error(const char *fmt, ...);
 
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int zrun,
                               cudaStream_t stream);
+void release_textures();
 fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t stream);
 fdk_status launch_count(const BpArgs &a, unsigned long long *count_dev, cudaStream_t stream);
 

@@ -9,7 +9,9 @@
 // so that u = U + u'_local / w.  In the hot loop every voxel is a small
 // integer offset d from the centre and the FP32 values stay small, which
 // keeps the detector coordinate accurate to ~1e-5 px instead of the ~1e-4 px
-// that a direct FP32 evaluation of P (X, 1) gives for 256 mm volumes.
+// that a direct FP32 evaluation of P (X, 1) gives for 256 mm volumes.  Only
+// the reference values and the two cancelling differences u' - U w and
+// v' - V w need FP64; the per-step coefficients are FP32 FMAs.
 //
 // The same prologue classifies the tile for the view from its eight corner
 // voxels (u and v of a box are extreme at its corners when w > 0): a tile
@@ -29,6 +31,15 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// floor() by a round-down add: for |x| < 2^22, x + 1.5*2^23 rounded toward
+// -inf is floor(x) + 1.5*2^23 exactly; its bit pattern is 0x4B400000 + floor(x).
+constexpr float kFloorMagic = 12582912.0f;
+constexpr int kFloorBits = 0x4B400000;
+// Flat tap index by float: for 0 <= n < 2^23, n + 2^23 is exact and its bit
+// pattern is 0x4B000000 + n.
+constexpr float kIndexMagic = 8388608.0f;
+constexpr unsigned kIndexBits = 0x4B000000u;
+
 // Fill tab[0..n_views) and the compacted list act[0..*n_act) of views whose
 // class is not kSkip; act[q] = view | class << 10.  All threads of the CTA
 // call this; it ends with __syncthreads().
@@ -39,45 +50,45 @@ __device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEn
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
     const Geom &g = a.g;
-    const double sx = g.vs[0], sy = g.vs[1], sz = g.vs[2];
-    const double Xc = (double)g.org[0] + (double)(x0 + BX / 2) * sx;
-    const double Yc = (double)g.org[1] + (double)(y0 + BY / 2) * sy;
-    const double Zc = (double)g.org[2] + (double)(z0 + R / 2) * sz;
+    const float sx = g.vs[0], sy = g.vs[1], sz = g.vs[2];
+    const double Xc = (double)g.org[0] + (double)(x0 + BX / 2) * (double)sx;
+    const double Yc = (double)g.org[1] + (double)(y0 + BY / 2) * (double)sy;
+    const double Zc = (double)g.org[2] + (double)(z0 + R / 2) * (double)sz;
     // corner offsets of the full tile box (every computed voxel, including
     // those past the volume edge that are computed but not stored)
     const float dx0 = (float)(-(BX / 2)), dx1 = (float)(BX - 1 - BX / 2);
     const float dy0 = (float)(-(BY / 2)), dy1 = (float)(BY - 1 - BY / 2);
     const float dz0 = (float)(-(R / 2)), dz1 = (float)(R - 1 - R / 2);
     const float eps = 1.0f / 64.0f;
+    const float Wf = (float)g.W;
 
     for (int v = tid; v < a.n_views; v += nthreads) {
-        double P[12];
+        float P[12];
         if (a.mats_dev) {
 #pragma unroll
-            for (int q = 0; q < 12; ++q) P[q] = (double)__ldg(a.mats_dev + 12 * v + q);
+            for (int q = 0; q < 12; ++q) P[q] = __ldg(a.mats_dev + 12 * v + q);
         } else {
 #pragma unroll
-            for (int q = 0; q < 12; ++q) P[q] = (double)a.mats[12 * v + q];
+            for (int q = 0; q < 12; ++q) P[q] = a.mats[12 * v + q];
         }
-        const double up = P[0] * Xc + P[1] * Yc + P[2] * Zc + P[3];
-        const double vp = P[4] * Xc + P[5] * Yc + P[6] * Zc + P[7];
-        const double wp = P[8] * Xc + P[9] * Yc + P[10] * Zc + P[11];
-        int U = 0, V = 0;
+        const double up = fma((double)P[0], Xc, fma((double)P[1], Yc, fma((double)P[2], Zc, (double)P[3])));
+        const double vp = fma((double)P[4], Xc, fma((double)P[5], Yc, fma((double)P[6], Zc, (double)P[7])));
+        const double wp = fma((double)P[8], Xc, fma((double)P[9], Yc, fma((double)P[10], Zc, (double)P[11])));
+        float Uf = 0.0f, Vf = 0.0f;
         if (wp > 0.0) {
-            float uf = (float)up / (float)wp, vf = (float)vp / (float)wp;
-            uf = fminf(fmaxf(uf, -1048576.0f), 1048576.0f);
-            vf = fminf(fmaxf(vf, -1048576.0f), 1048576.0f);
-            U = __float2int_rn(uf);
-            V = __float2int_rn(vf);
+            const float iw = 1.0f / (float)wp;
+            Uf = rintf(fminf(fmaxf((float)up * iw, -1048576.0f), 1048576.0f));
+            Vf = rintf(fminf(fmaxf((float)vp * iw, -1048576.0f), 1048576.0f));
         }
-        const double dU = (double)U, dV = (double)V;
         ViewEntry e;
-        e.ru = make_float4((float)(up - dU * wp), (float)((P[0] - dU * P[8]) * sx),
-                           (float)((P[1] - dU * P[9]) * sy), (float)((P[2] - dU * P[10]) * sz));
-        e.rv = make_float4((float)(vp - dV * wp), (float)((P[4] - dV * P[8]) * sx),
-                           (float)((P[5] - dV * P[9]) * sy), (float)((P[6] - dV * P[10]) * sz));
-        e.rw = make_float4((float)wp, (float)(P[8] * sx), (float)(P[9] * sy), (float)(P[10] * sz));
-        e.off = make_float4((float)U + 1.0f, (float)V + 1.0f, __int_as_float(U), __int_as_float(V));
+        e.a = make_float4((float)fma(-(double)Uf, wp, up), (float)fma(-(double)Vf, wp, vp),
+                          fmaf(-Uf, P[8], P[0]) * sx, fmaf(-Vf, P[8], P[4]) * sx);
+        e.b = make_float4(fmaf(-Uf, P[9], P[1]) * sy, fmaf(-Vf, P[9], P[5]) * sy,
+                          fmaf(-Uf, P[10], P[2]) * sz, fmaf(-Vf, P[10], P[6]) * sz);
+        e.w = make_float4((float)wp, P[8] * sx, P[9] * sy, P[10] * sz);
+        // flat index offset of the cell (U, V) plus the index magic; exact
+        // whenever the cell is inside the image and W*H < 2^23
+        e.o = make_float4(Uf, Vf, fmaf(Vf, Wf, Uf) + kIndexMagic, 0.0f);
 
         // classify from the 8 corners
         float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
@@ -87,12 +98,13 @@ __device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEn
             const float dx = (c & 1) ? dx1 : dx0;
             const float dy = (c & 2) ? dy1 : dy0;
             const float dz = (c & 4) ? dz1 : dz0;
-            const float wl = fmaf(dz, e.rw.w, fmaf(dy, e.rw.z, fmaf(dx, e.rw.y, e.rw.x)));
-            const float ul = fmaf(dz, e.ru.w, fmaf(dy, e.ru.z, fmaf(dx, e.ru.y, e.ru.x)));
-            const float vl = fmaf(dz, e.rv.w, fmaf(dy, e.rv.z, fmaf(dx, e.rv.y, e.rv.x)));
+            const float wl = fmaf(dz, e.w.w, fmaf(dy, e.w.z, fmaf(dx, e.w.y, e.w.x)));
+            const float ul = fmaf(dz, e.b.z, fmaf(dy, e.b.x, fmaf(dx, e.a.z, e.a.x)));
+            const float vl = fmaf(dz, e.b.w, fmaf(dy, e.b.y, fmaf(dx, e.a.w, e.a.y)));
             if (wl > 0.0f) {
                 ++npos;
-                const float uu = ul / wl + (float)U, vv = vl / wl + (float)V;
+                const float r = rcp_approx(wl);
+                const float uu = fmaf(ul, r, Uf), vv = fmaf(vl, r, Vf);
                 umin = fminf(umin, uu); umax = fmaxf(umax, uu);
                 vmin = fminf(vmin, vv); vmax = fmaxf(vmax, vv);
             }
@@ -102,10 +114,10 @@ __device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEn
             c = kSkip;                      // w <= 0 on the whole tile (w is linear)
         } else if (npos < 8) {
             c = kGeneral;                   // tile crosses the source plane: per-voxel w test
-        } else if (umax < -1.0f - eps || umin > (float)g.W + eps ||
+        } else if (umax < -1.0f - eps || umin > Wf + eps ||
                    vmax < -1.0f - eps || vmin > (float)g.H + eps) {
             c = kSkip;                      // every tap of every voxel is off the detector
-        } else if (umin >= eps && umax <= (float)(g.W - 1) - eps &&
+        } else if (umin >= eps && umax <= Wf - 1.0f - eps &&
                    vmin >= eps && vmax <= (float)(g.H - 1) - eps) {
             c = kInterior;                  // all four taps inside for every voxel
         } else {

@@ -46,7 +46,7 @@ def ragged():
     return synth.make_scan(synth.preset("small", nx=37, ny=29, nz=21), device="cuda")
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_AUTO])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_AUTO])
 @pytest.mark.parametrize("zrun", [4, 8, 16])
 def test_ragged_parity(ragged, fetch, zrun):
     ref = _oracle(ragged)
@@ -88,26 +88,51 @@ def test_small_volumes(dims):
         assert_parity(ref, got, what=str(dims))
 
 
-def test_more_views_than_one_pass():
-    # 600 views > 512 per kernel pass: two passes accumulate
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+def test_more_views_than_one_pass(fetch):
+    # 600 views > 512 per kernel pass: two passes accumulate (the texture
+    # path re-stages its arrays between the passes)
     s = synth.make_scan(synth.preset("small", n_views=600, det_w=40, det_h=32, nx=20, ny=18, nz=10),
                         device="cuda")
     ref = _oracle(s)
-    got = _gpu_bp(s).cpu().numpy()
+    got = _gpu_bp(s, fetch=fetch).cpu().numpy()
     assert_parity(ref, got)
 
 
-def test_source_inside_volume():
+def test_texture_staging_shared_across_streams(ragged):
+    """Two streams back-project different data through the same cached
+    staging arrays; each result must still match its own oracle."""
+    p2 = (ragged["proj"] * -0.5).contiguous()
+    ref1, ref2 = _oracle(ragged), _oracle(ragged, proj=p2)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    v1 = torch.zeros((21, 29, 37), device="cuda")
+    v2 = torch.zeros_like(v1)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        with torch.cuda.stream(s1):
+            fdk.fdk_backproject(v1, ragged["proj"], ragged["mats"], ragged["voxel_size"],
+                                ragged["origin"], fetch=fdk.FETCH_TEX)
+        with torch.cuda.stream(s2):
+            fdk.fdk_backproject(v2, p2, ragged["mats"], ragged["voxel_size"], ragged["origin"],
+                                fetch=fdk.FETCH_TEX)
+    torch.cuda.synchronize()
+    assert_parity(3 * ref1, v1.cpu().numpy())
+    assert_parity(3 * ref2, v2.cpu().numpy())
+
+
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+def test_source_inside_volume(fetch):
     """Source at 150 mm inside a 400 mm volume: some tiles straddle the
     source plane (w <= 0 voxels contribute nothing)."""
     s = synth.make_scan(synth.preset("small", nx=40, ny=40, nz=8, voxel=10.0, sid=150.0, sdd=300.0),
                         device="cuda")
     ref = _oracle(s)
-    got = _gpu_bp(s).cpu().numpy()
+    got = _gpu_bp(s, fetch=fetch).cpu().numpy()
     assert_parity(ref, got)
 
 
-def test_orthographic_identity_exact():
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+def test_orthographic_identity_exact(fetch):
     """w = 1, u = x, v = y: each z slice is a copy of the image (zero past
     the detector edge)."""
     rng = np.random.default_rng(0)
@@ -118,7 +143,7 @@ def test_orthographic_identity_exact():
     P[0, 5] = 1.0
     P[0, 11] = 1.0
     vol = torch.zeros((9, 60, 80), device="cuda")
-    fdk.fdk_backproject(vol, img, P, (1, 1, 1), (0, 0, 0))
+    fdk.fdk_backproject(vol, img, P, (1, 1, 1), (0, 0, 0), fetch=fetch)
     torch.cuda.synchronize()
     v = vol.cpu().numpy()
     for z in range(9):
@@ -126,23 +151,30 @@ def test_orthographic_identity_exact():
         assert np.all(v[z, H:, :] == 0) and np.all(v[z, :, W:] == 0)
 
 
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
-def test_half_storage(ragged, dtype):
+def test_half_storage(ragged, dtype, fetch):
     """Projections stored as FP16/BF16; interpolation and accumulation in
     FP32.  The oracle sees the same stored values (exactly converted)."""
     p16 = ragged["proj"].to(dtype)
     ref = _oracle(ragged, proj=p16)
-    got = _gpu_bp(ragged, proj=p16).cpu().numpy()
-    assert_parity(ref, got, what=str(dtype))
+    got = _gpu_bp(ragged, proj=p16, fetch=fetch).cpu().numpy()
+    assert_parity(ref, got, what=f"{dtype} fetch={fetch}")
 
 
-def test_full_128_cube_496_views():
-    """The 128^3 x 496-view, 1248 x 960 workload, whole volume."""
+@pytest.fixture(scope="module")
+def fdk128():
     s = synth.make_scan(synth.PRESETS["fdk128"], device="cuda")
-    ref = _oracle(s)
-    got = _gpu_bp(s).cpu().numpy()
+    return s, _oracle(s)
+
+
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+def test_full_128_cube_496_views(fdk128, fetch):
+    """The 128^3 x 496-view, 1248 x 960 workload, whole volume."""
+    s, ref = fdk128
+    got = _gpu_bp(s, fetch=fetch).cpu().numpy()
     rel, p = assert_parity(ref, got, what="fdk128")
-    print(f"fdk128: max|diff|/max|f| = {rel:.3e}, PSNR = {p:.1f} dB")
+    print(f"fdk128 fetch={fetch}: max|diff|/max|f| = {rel:.3e}, PSNR = {p:.1f} dB")
 
 
 def test_sampled_512_cube_496_views():
