@@ -234,7 +234,7 @@ __device__ __forceinline__ void view_tex(float (&acc)[R], const ViewEntry &e, fl
 }
 
 // CTA tile BX x BY x R; warps cover WX x (32/WX) voxel patches in (x, y).
-template <int BX, int BY, int WX, int R, int MINB, int FETCH, typename T, bool FIDX>
+template <int BX, int BY, int WX, int R, int MINB, int KCHUNK, int FETCH, typename T, bool FIDX>
 __global__ void __launch_bounds__(BX * BY, MINB)
 fdk_bp_kernel(const __grid_constant__ BpArgs a)
 {
@@ -242,14 +242,12 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
     static_assert(R % 2 == 0, "z-run must be even (voxel pairs)");
     constexpr int WY = 32 / WX;
     constexpr int WPX = BX / WX;
-    __shared__ ViewEntry tab[KMAX];
-    __shared__ unsigned char cls[KMAX];
-    __shared__ unsigned short act[KMAX];
+    __shared__ ViewEntry tab[KCHUNK];
+    __shared__ unsigned char cls[KCHUNK];
+    __shared__ unsigned short act[KCHUNK];
     __shared__ int n_act;
 
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * R;
-    build_view_table<BX, BY, R>(a, x0, y0, z0, tab, cls, act, &n_act);
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = (warp % WPX) * WX + (lane % WX);
     const int ly = (warp / WPX) * WY + (lane / WX);
@@ -261,21 +259,27 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0f;
 
-    const int n = n_act;
-    for (int q = 0; q < n; ++q) {
-        const int ev = act[q];
-        const int v = ev & 1023, c = ev >> 10;
-        const ViewEntry e = tab[v];
-        if (FETCH == kTex) {
-            const cudaTextureObject_t tex = (cudaTextureObject_t)a.tex[v];
-            if (c != kGeneral) view_tex<R, T, false>(acc, e, dxf, dyf, tex, W, H);
-            else view_tex<R, T, true>(acc, e, dxf, dyf, tex, W, H);
-        } else {
-            const T *img = proj + (long long)v * a.plane;
-            if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
-            else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
-            else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
+    for (int v0 = 0; v0 < a.n_views; v0 += KCHUNK) {
+        const int nv = min(KCHUNK, a.n_views - v0);
+        build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act);
+        const int n = n_act;
+        for (int q = 0; q < n; ++q) {
+            const int ev = act[q];
+            const int lv = ev & 1023, c = ev >> 10;
+            const int v = v0 + lv;
+            const ViewEntry e = tab[lv];
+            if (FETCH == kTex) {
+                const cudaTextureObject_t tex = (cudaTextureObject_t)a.tex[v];
+                if (c != kGeneral) view_tex<R, T, false>(acc, e, dxf, dyf, tex, W, H);
+                else view_tex<R, T, true>(acc, e, dxf, dyf, tex, W, H);
+            } else {
+                const T *img = proj + (long long)v * a.plane;
+                if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
+                else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
+                else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
+            }
         }
+        __syncthreads();   // the next chunk overwrites the table
     }
 
     const int x = x0 + lx, y = y0 + ly;
@@ -293,8 +297,9 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
 template <int BX, int BY, int WX, int R, int MINB, int FETCH, typename T, bool FIDX>
 static fdk_status launch_one(const BpArgs &a, cudaStream_t s)
 {
+    constexpr int KCHUNK = 128;
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + R - 1) / R);
-    fdk_bp_kernel<BX, BY, WX, R, MINB, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
+    fdk_bp_kernel<BX, BY, WX, R, MINB, KCHUNK, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error("back-projection launch failed: %s", cudaGetErrorString(err));

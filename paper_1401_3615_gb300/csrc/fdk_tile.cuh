@@ -40,12 +40,15 @@ constexpr int kFloorBits = 0x4B400000;
 constexpr float kIndexMagic = 8388608.0f;
 constexpr unsigned kIndexBits = 0x4B000000u;
 
-// Fill tab[0..n_views) and the compacted list act[0..*n_act) of views whose
-// class is not kSkip; act[q] = view | class << 10.  All threads of the CTA
-// call this; it ends with __syncthreads().
+// Fill tab[0..nv) for views v0..v0+nv of the pass and the compacted list
+// act[0..*n_act) of those whose class is not kSkip; act[q] = (v - v0) |
+// class << 10.  All threads of the CTA call this; it ends with
+// __syncthreads().  Tables are built in chunks of views so that the shared
+// memory they take stays small and the rest of the SM's L1 holds image data.
 template <int BX, int BY, int R>
-__device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEntry *tab,
-                                 unsigned char *cls, unsigned short *act, int *n_act)
+__device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0, int z0,
+                                 ViewEntry *tab, unsigned char *cls, unsigned short *act,
+                                 int *n_act)
 {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
@@ -62,7 +65,8 @@ __device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEn
     const float eps = 1.0f / 64.0f;
     const float Wf = (float)g.W;
 
-    for (int v = tid; v < a.n_views; v += nthreads) {
+    for (int lv = tid; lv < nv; lv += nthreads) {
+        const int v = v0 + lv;
         float P[12];
         if (a.mats_dev) {
 #pragma unroll
@@ -123,15 +127,15 @@ __device__ void build_view_table(const BpArgs &a, int x0, int y0, int z0, ViewEn
         } else {
             c = kBoundary;
         }
-        tab[v] = e;
-        cls[v] = (unsigned char)c;
+        tab[lv] = e;
+        cls[lv] = (unsigned char)c;
     }
     __syncthreads();
     if (tid < 32) {
         int count = 0;
-        for (int base = 0; base < a.n_views; base += 32) {
+        for (int base = 0; base < nv; base += 32) {
             const int v = base + tid;
-            const int c = (v < a.n_views) ? (int)cls[v] : 0;
+            const int c = (v < nv) ? (int)cls[v] : 0;
             const unsigned m = __ballot_sync(0xffffffffu, c != kSkip);
             if (c != kSkip) {
                 const int pos = count + __popc(m & ((1u << tid) - 1u));
