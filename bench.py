@@ -198,7 +198,7 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     def e2e_step():
         d_proj.copy_(h_proj, non_blocking=True)
         vol.zero_()
-        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
+        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
         h_vol.copy_(vol, non_blocking=True)
 
     e2e_step()
@@ -246,7 +246,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        fdk.fdk_backproject(vol, proj, mats, vs, org, fetch=args.fetch, zrun=args.zrun)
+        fdk.fdk_backproject(vol, proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -320,7 +320,7 @@ def run_ours(args):
                        "updates_per_step": upd_full, "clipped_updates_per_step": upd_clip,
                        "l2": (f"inputs larger than L2 (projections {proj.numel() * proj.element_size() / 1e9:.2f} GB, "
                               f"volume {vol.numel() * 4 / 2**20:.0f} MiB)"),
-                       "fetch": args.fetch, "zrun": args.zrun or 8,
+                       "fetch": args.fetch, "tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="fdk512")
     ap.add_argument("--fetch", type=int, default=0)
-    ap.add_argument("--zrun", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")

@@ -24,9 +24,12 @@
  *
  * Memory: every buffer is owned by the caller.  "device" means a pointer the
  * current CUDA device can dereference (cudaMalloc, torch CUDA tensors).  The
- * plain entry points allocate no device memory per call.  Calls enqueue
- * kernels on opts->stream and return; asynchronous faults surface at the
- * caller's next synchronisation.
+ * QUAD and TEX fetch paths stage the images in library-owned device buffers
+ * that are allocated on first use for a detector shape, cached per device and
+ * reused by later calls (fdk_release() frees them); calls that share one
+ * cache entry are ordered by an event, whatever their streams.  The LDG path
+ * allocates nothing.  Calls enqueue kernels on opts->stream and return;
+ * asynchronous faults surface at the caller's next synchronisation.
  *
  * Errors: argument problems return FDK_ERR_INVALID_ARG before anything is
  * enqueued; fdk_last_error() then gives a message (thread-local).  No C++
@@ -69,8 +72,11 @@ typedef enum fdk_dtype {
 typedef enum fdk_fetch {
     FDK_FETCH_AUTO = 0,
     FDK_FETCH_LDG = 1,         /* read-only global loads, bounds checked per tile class */
-    FDK_FETCH_TEX = 2          /* 2x2 texture gather with zero border (taps in FP32); the
+    FDK_FETCH_TEX = 2,         /* 2x2 texture gather with zero border (taps in FP32); the
                                   images are first copied into cached CUDA arrays */
+    FDK_FETCH_QUAD = 3         /* one load per voxel from a zero-bordered "quad image" (each
+                                  cell holds its 2x2 taps) built on the device per call in a
+                                  cached staging buffer: 16 B per pixel (FP32), 8 B (FP16/BF16) */
 } fdk_fetch;
 
 /* Optional knobs; pass NULL for defaults.  Zero in any field means default. */
@@ -79,7 +85,10 @@ typedef struct fdk_opts {
     int32_t matrices_on_device;  /* 1: `matrices` is a device pointer; 0: host */
     void *stream;                /* cudaStream_t; NULL = the legacy default stream */
     int32_t fetch;               /* fdk_fetch */
-    int32_t zrun;                /* voxels per thread along z: 4, 8 or 16 */
+    int32_t tile;                /* CTA tile variant 0..7 (x by y voxels, z-run per thread):
+                                    0: default (currently 16x16, 8)
+                                    1: 16x16, 8   2: 32x16, 4   3: 32x16, 8   4: 32x8, 4
+                                    5: 16x16, 4   6: 32x8, 16   7: 16x16, 16 */
     int32_t reserved[10];        /* must be zero */
 } fdk_opts;
 

@@ -66,10 +66,9 @@ static fdk_status check_opts(const fdk_opts *o)
         return fail(FDK_ERR_INVALID_ARG, "unknown proj_dtype");
     if (o->matrices_on_device != 0 && o->matrices_on_device != 1)
         return fail(FDK_ERR_INVALID_ARG, "matrices_on_device must be 0 or 1");
-    if (o->fetch < FDK_FETCH_AUTO || o->fetch > FDK_FETCH_TEX)
+    if (o->fetch < FDK_FETCH_AUTO || o->fetch > FDK_FETCH_QUAD)
         return fail(FDK_ERR_INVALID_ARG, "unknown fetch path");
-    if (o->zrun != 0 && o->zrun != 4 && o->zrun != 8 && o->zrun != 16)
-        return fail(FDK_ERR_INVALID_ARG, "zrun must be 0, 4, 8 or 16");
+    if (o->tile < 0 || o->tile > 7) return fail(FDK_ERR_INVALID_ARG, "tile must be 0..7");
     for (int q = 0; q < 10; ++q)
         if (o->reserved[q] != 0) return fail(FDK_ERR_INVALID_ARG, "reserved option fields must be zero");
     return FDK_OK;
@@ -210,6 +209,80 @@ static fdk_status tex_stage_get(int dev, int W, int H, int dtype, int n, TexStag
     return FDK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Quad staging: one device buffer of quad images per (device, W, H, dtype),
+// grown to the largest pass seen, reused by later calls and ordered across
+// streams by an event recorded after each call's kernels.
+struct QuadStage {
+    int dev, W, H, dtype;
+    void *buf = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+};
+
+static std::mutex g_quad_mu;
+static std::vector<std::unique_ptr<QuadStage>> g_quad;
+
+// Quad cell indices, including those of boundary tiles whose reference cell
+// lies up to 64 cells off the image, must be exact FP32 integers.
+static bool quad_supported(int W, int H)
+{
+    return (long long)(W + 3 + 130) * (H + 3 + 130) < (1LL << 23);
+}
+
+// Caller holds g_quad_mu.
+static fdk_status quad_stage_get(int dev, int W, int H, int dtype, int n, QuadStage **out)
+{
+    QuadStage *t = nullptr;
+    for (auto &p : g_quad)
+        if (p->dev == dev && p->W == W && p->H == H && p->dtype == dtype) t = p.get();
+    if (!t) {
+        g_quad.emplace_back(new QuadStage());
+        t = g_quad.back().get();
+        t->dev = dev; t->W = W; t->H = H; t->dtype = dtype;
+    }
+    if (!t->done && cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "cudaEventCreate failed");
+    }
+    const size_t need = (size_t)(W + 3) * (size_t)(H + 3) * quad_elem_size(dtype) * (size_t)n;
+    if (t->bytes < need) {
+        if (t->buf) {
+            cudaEventSynchronize(t->done);   // the old buffer may still be read
+            cudaFree(t->buf);
+            t->buf = nullptr;
+            t->bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&t->buf, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("quad staging: cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? FDK_ERR_OOM : FDK_ERR_CUDA;
+        }
+        t->bytes = need;
+    }
+    *out = t;
+    return FDK_OK;
+}
+
+static void release_quads()
+{
+    std::lock_guard<std::mutex> lk(g_quad_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &p : g_quad) {
+        cudaSetDevice(p->dev);
+        if (p->done) {
+            cudaEventSynchronize(p->done);
+            cudaEventDestroy(p->done);
+        }
+        if (p->buf) cudaFree(p->buf);
+    }
+    g_quad.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
 void release_textures()
 {
     std::lock_guard<std::mutex> lk(g_tex_mu);
@@ -235,7 +308,11 @@ const char *fdk_last_error(void) { return g_err; }
 
 int32_t fdk_version(void) { return 1; }
 
-void fdk_release(void) { release_textures(); }
+void fdk_release(void)
+{
+    release_textures();
+    release_quads();
+}
 
 fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float voxel_size[3],
                            const float origin[3], const void *projections, const int32_t det[2],
@@ -264,33 +341,36 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     int dev = 0;
     cudaGetDevice(&dev);
 
-    // texture path only on request: on GB300 the 2x2 gather rate of the
-    // texture units is below what the LDG path reaches
-    bool use_tex = false;
+    // texture and quad paths only on request: on GB300 both measure slower
+    // than the LDG path at the 512^3 x 496-view, 1248 x 960 workload
+    bool use_tex = false, use_quad = false;
     TexStage *stage = nullptr;
+    QuadStage *qstage = nullptr;
     std::unique_lock<std::mutex> lk(g_tex_mu, std::defer_lock);
+    std::unique_lock<std::mutex> qlk(g_quad_mu, std::defer_lock);
+    const int n_pass = n_views < KMAX ? n_views : KMAX;
     if (o->fetch == FDK_FETCH_TEX) {
-        if (!tex_supported(dev, g.W, g.H)) {
-            if (o->fetch == FDK_FETCH_TEX)
-                return fail(FDK_ERR_UNSUPPORTED, "detector exceeds the device's texture-gather size");
-        } else {
-            lk.lock();
-            st = tex_stage_get(dev, g.W, g.H, o->proj_dtype, n_views < KMAX ? n_views : KMAX, &stage);
-            if (st == FDK_OK) {
-                use_tex = true;
-            } else if (o->fetch == FDK_FETCH_TEX) {
-                return st;
-            } else {
-                lk.unlock();
-                g_err[0] = 0;   // AUTO: fall back to the LDG path
-            }
-        }
+        if (!tex_supported(dev, g.W, g.H))
+            return fail(FDK_ERR_UNSUPPORTED, "detector exceeds the device's texture-gather size");
+        lk.lock();
+        if ((st = tex_stage_get(dev, g.W, g.H, o->proj_dtype, n_pass, &stage))) return st;
+        use_tex = true;
+    } else if (o->fetch == FDK_FETCH_QUAD) {
+        if (!quad_supported(g.W, g.H))
+            return fail(FDK_ERR_UNSUPPORTED, "detector too large for quad images (2^23 cells)");
+        qlk.lock();
+        if ((st = quad_stage_get(dev, g.W, g.H, o->proj_dtype, n_pass, &qstage))) return st;
+        use_quad = true;
     }
-    if (use_tex && cudaStreamWaitEvent(s, stage->done, 0) != cudaSuccess) {
+    cudaEvent_t guard = use_tex ? stage->done : (use_quad ? qstage->done : nullptr);
+    if (guard && cudaStreamWaitEvent(s, guard, 0) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_CUDA, "cudaStreamWaitEvent failed");
     }
 
+    int fetch = 1;
+    if (use_tex) fetch = 2;
+    if (use_quad) fetch = 3;
     for (int v0 = 0; v0 < n_views; v0 += KMAX) {
         const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
         a.g = g;
@@ -298,6 +378,9 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         a.proj = static_cast<const char *>(projections) + (size_t)v0 * plane * esz;
         a.plane = plane;
         a.n_views = nv;
+        a.quads = nullptr;
+        a.qpitch = g.W + 3;
+        a.qplane = (long long)(g.W + 3) * (g.H + 3);
         if (o->matrices_on_device) {
             a.mats_dev = matrices + (size_t)v0 * 12;
         } else {
@@ -317,10 +400,13 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
                 a.tex[k] = (unsigned long long)stage->texs[k];
             }
         }
-        if ((st = launch_backproject(a, use_tex ? 2 : 1, o->proj_dtype, o->zrun ? o->zrun : 8, s)))
-            return st;
+        if (use_quad) {
+            if ((st = launch_make_quads(a.proj, qstage->buf, nv, g.W, g.H, o->proj_dtype, s))) return st;
+            a.quads = qstage->buf;
+        }
+        if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
     }
-    if (use_tex) cudaEventRecord(stage->done, s);
+    if (guard) cudaEventRecord(guard, s);
     return FDK_OK;
 }
 

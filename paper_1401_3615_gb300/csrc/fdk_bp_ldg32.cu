@@ -1,0 +1,13 @@
+// Instantiations of the back-projection kernel: LDG fetch, float storage.
+#include "fdk_bp_kernel.cuh"
+
+namespace fdk {
+
+fdk_status launch_bp_ldg_f32(const BpArgs &a, int tile, cudaStream_t s)
+{
+    // the float flat index is exact while every tap index is below 2^23
+    if ((long long)a.g.W * (a.g.H + 1) < (1LL << 23)) return launch_tiles<kLdg, float, true>(a, tile, s);
+    return launch_tiles<kLdg, float, false>(a, tile, s);
+}
+
+}  // namespace fdk

@@ -29,6 +29,9 @@ struct BpArgs {
     float *vol;
     const void *proj;          // first image of this pass
     const float *mats_dev;     // device matrices of this pass, or nullptr
+    const void *quads;         // quad images of this pass (quad fetch path), or nullptr
+    int qpitch;                // quad cells per quad-image row: W + 3
+    long long qplane;          // quad cells per quad image: (W + 3) * (H + 3)
     long long plane;           // W*H elements per image
     int n_views;               // views in this pass (<= KMAX)
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
@@ -44,7 +47,7 @@ struct __align__(16) ViewEntry {
     float4 a;    // (c_u, c_v, gx_u, gx_v): value at the tile centre, step in x
     float4 b;    // (gy_u, gy_v, gz_u, gz_v): steps in y and z
     float4 w;    // (c_w, gx_w, gy_w, gz_w)
-    float4 o;    // (U, V, V*W + U + 2^23, 0)
+    float4 o;    // (U, V, V*W + U + 2^23, (V+2)*(W+3) + U + 2 + 2^23)
 };
 
 enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
@@ -52,9 +55,12 @@ enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
 // Thread-local error message setter (fdk_api.cu).
 void set_error(const char *fmt, ...);
 
-fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int zrun,
+fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile,
                               cudaStream_t stream);
 void release_textures();
+size_t quad_elem_size(int dtype);
+fdk_status launch_make_quads(const void *proj, void *quads, int n, int W, int H, int dtype,
+                             cudaStream_t stream);
 fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t stream);
 fdk_status launch_count(const BpArgs &a, unsigned long long *count_dev, cudaStream_t stream);
 

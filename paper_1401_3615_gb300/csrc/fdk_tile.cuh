@@ -90,9 +90,11 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
         e.b = make_float4(fmaf(-Uf, P[9], P[1]) * sy, fmaf(-Vf, P[9], P[5]) * sy,
                           fmaf(-Uf, P[10], P[2]) * sz, fmaf(-Vf, P[10], P[6]) * sz);
         e.w = make_float4((float)wp, P[8] * sx, P[9] * sy, P[10] * sz);
-        // flat index offset of the cell (U, V) plus the index magic; exact
-        // whenever the cell is inside the image and W*H < 2^23
-        e.o = make_float4(Uf, Vf, fmaf(Vf, Wf, Uf) + kIndexMagic, 0.0f);
+        // flat index offsets of the cell (U, V) in the image and in the quad
+        // image, plus the index magic (exact while the images are below 2^23
+        // cells and the cell lies in or near them)
+        e.o = make_float4(Uf, Vf, fmaf(Vf, Wf, Uf) + kIndexMagic,
+                          fmaf(Vf + 2.0f, Wf + 3.0f, Uf + 2.0f) + kIndexMagic);
 
         // classify from the 8 corners
         float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
@@ -127,6 +129,11 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
         } else {
             c = kBoundary;
         }
+        // boundary tiles whose reference cell lies far off the image (only
+        // near the source plane) take the fully checked path, so the quad
+        // index offset in e.o.w stays an exact FP32 integer
+        if (c == kBoundary && (Uf < -64.0f || Uf > Wf + 64.0f || Vf < -64.0f || Vf > (float)g.H + 64.0f))
+            c = kGeneral;
         tab[lv] = e;
         cls[lv] = (unsigned char)c;
     }

@@ -18,7 +18,7 @@ from . import build as _build
 
 FDK_OK, FDK_ERR_INVALID_ARG, FDK_ERR_UNSUPPORTED, FDK_ERR_OOM, FDK_ERR_CUDA, FDK_ERR_TIMEOUT = range(6)
 FDK_F32, FDK_BF16, FDK_F16 = 0, 1, 2
-FETCH_AUTO, FETCH_LDG, FETCH_TEX = 0, 1, 2
+FETCH_AUTO, FETCH_LDG, FETCH_TEX, FETCH_QUAD = 0, 1, 2, 3
 _STATUS = {0: "FDK_OK", 1: "FDK_ERR_INVALID_ARG", 2: "FDK_ERR_UNSUPPORTED", 3: "FDK_ERR_OOM",
            4: "FDK_ERR_CUDA", 5: "FDK_ERR_TIMEOUT"}
 _DTYPES = {torch.float32: FDK_F32, torch.bfloat16: FDK_BF16, torch.float16: FDK_F16}
@@ -32,7 +32,7 @@ class FdkError(RuntimeError):
 
 class fdk_opts(ctypes.Structure):
     _fields_ = [("proj_dtype", ctypes.c_int32), ("matrices_on_device", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("fetch", ctypes.c_int32), ("zrun", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("fetch", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 10)]
 
 
@@ -110,14 +110,14 @@ def _mats(matrices, n_views: int):
     return m, m.ctypes.data, 0
 
 
-def _opts(dtype: int, mats_dev: int, stream, fetch: int, zrun: int) -> fdk_opts:
+def _opts(dtype: int, mats_dev: int, stream, fetch: int, tile: int) -> fdk_opts:
     o = fdk_opts()
     o.proj_dtype = dtype
     o.matrices_on_device = mats_dev
     o.stream = stream if isinstance(stream, int) else (
         (stream or torch.cuda.current_stream()).cuda_stream)
     o.fetch = fetch
-    o.zrun = zrun
+    o.tile = tile
     return o
 
 
@@ -128,7 +128,7 @@ def _geom(voxel_size, origin):
 
 
 def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, voxel_size, origin,
-                    *, fetch: int = FETCH_AUTO, zrun: int = 0, stream=None) -> torch.Tensor:
+                    *, fetch: int = FETCH_AUTO, tile: int = 0, stream=None) -> torch.Tensor:
     """volume[nz,ny,nx] (CUDA FP32) += back-projection of projections[n,H,W]
     (CUDA FP32/BF16/FP16) with per-view row-major 3x4 matrices (host array or
     CUDA tensor).  Returns ``volume``."""
@@ -142,7 +142,7 @@ def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, v
     m, mptr, mdev = _mats(matrices, n)
     nz, ny, nx = volume.shape
     vs, org = _geom(voxel_size, origin)
-    o = _opts(_DTYPES[projections.dtype], mdev, stream, fetch, zrun)
+    o = _opts(_DTYPES[projections.dtype], mdev, stream, fetch, tile)
     lib = _load()
     st = lib.fdk_backproject(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
                              _i32_2(projections.shape[2], projections.shape[1]), mptr, n,

@@ -72,7 +72,7 @@ def test_invalid_arguments_rejected(kw, msg):
 
 def test_bad_options_rejected():
     for field, val, msg in [("proj_dtype", 7, "proj_dtype"), ("matrices_on_device", 2, "matrices_on_device"),
-                            ("fetch", 9, "fetch"), ("zrun", 5, "zrun")]:
+                            ("fetch", 9, "fetch"), ("tile", 8, "tile"), ("tile", -1, "tile")]:
         o = fdk.fdk_opts()
         setattr(o, field, val)
         assert _call_bp(opts=o) == fdk.FDK_ERR_INVALID_ARG

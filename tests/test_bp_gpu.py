@@ -21,14 +21,14 @@ pytestmark = pytest.mark.gpu
 NCPU = os.cpu_count() or 1
 
 
-def _gpu_bp(scan, proj=None, fetch=fdk.FETCH_AUTO, zrun=0, mats=None, vol=None):
+def _gpu_bp(scan, proj=None, fetch=fdk.FETCH_AUTO, tile=0, mats=None, vol=None):
     p = scan["proj"] if proj is None else proj
     p = p.cuda() if not p.is_cuda else p
     dims = scan["dims"]
     if vol is None:
         vol = torch.zeros((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32, device="cuda")
     fdk.fdk_backproject(vol, p.contiguous(), scan["mats"] if mats is None else mats,
-                        scan["voxel_size"], scan["origin"], fetch=fetch, zrun=zrun)
+                        scan["voxel_size"], scan["origin"], fetch=fetch, tile=tile)
     torch.cuda.synchronize()
     return vol
 
@@ -46,12 +46,12 @@ def ragged():
     return synth.make_scan(synth.preset("small", nx=37, ny=29, nz=21), device="cuda")
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_AUTO])
-@pytest.mark.parametrize("zrun", [4, 8, 16])
-def test_ragged_parity(ragged, fetch, zrun):
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD, fdk.FETCH_AUTO])
+@pytest.mark.parametrize("tile", range(8))
+def test_ragged_parity(ragged, fetch, tile):
     ref = _oracle(ragged)
-    got = _gpu_bp(ragged, fetch=fetch, zrun=zrun).cpu().numpy()
-    assert_parity(ref, got, what=f"fetch={fetch} zrun={zrun}")
+    got = _gpu_bp(ragged, fetch=fetch, tile=tile).cpu().numpy()
+    assert_parity(ref, got, what=f"fetch={fetch} tile={tile}")
 
 
 def test_accumulates(ragged):
@@ -88,7 +88,7 @@ def test_small_volumes(dims):
         assert_parity(ref, got, what=str(dims))
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD])
 def test_more_views_than_one_pass(fetch):
     # 600 views > 512 per kernel pass: two passes accumulate (the texture
     # path re-stages its arrays between the passes)
@@ -99,9 +99,10 @@ def test_more_views_than_one_pass(fetch):
     assert_parity(ref, got)
 
 
-def test_texture_staging_shared_across_streams(ragged):
+@pytest.mark.parametrize("fetch", [fdk.FETCH_TEX, fdk.FETCH_QUAD])
+def test_staging_shared_across_streams(ragged, fetch):
     """Two streams back-project different data through the same cached
-    staging arrays; each result must still match its own oracle."""
+    staging buffers; each result must still match its own oracle."""
     p2 = (ragged["proj"] * -0.5).contiguous()
     ref1, ref2 = _oracle(ragged), _oracle(ragged, proj=p2)
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
@@ -111,16 +112,16 @@ def test_texture_staging_shared_across_streams(ragged):
     for _ in range(3):
         with torch.cuda.stream(s1):
             fdk.fdk_backproject(v1, ragged["proj"], ragged["mats"], ragged["voxel_size"],
-                                ragged["origin"], fetch=fdk.FETCH_TEX)
+                                ragged["origin"], fetch=fetch)
         with torch.cuda.stream(s2):
             fdk.fdk_backproject(v2, p2, ragged["mats"], ragged["voxel_size"], ragged["origin"],
-                                fetch=fdk.FETCH_TEX)
+                                fetch=fetch)
     torch.cuda.synchronize()
     assert_parity(3 * ref1, v1.cpu().numpy())
     assert_parity(3 * ref2, v2.cpu().numpy())
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD])
 def test_source_inside_volume(fetch):
     """Source at 150 mm inside a 400 mm volume: some tiles straddle the
     source plane (w <= 0 voxels contribute nothing)."""
@@ -131,7 +132,7 @@ def test_source_inside_volume(fetch):
     assert_parity(ref, got)
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD])
 def test_orthographic_identity_exact(fetch):
     """w = 1, u = x, v = y: each z slice is a copy of the image (zero past
     the detector edge)."""
@@ -151,7 +152,7 @@ def test_orthographic_identity_exact(fetch):
         assert np.all(v[z, H:, :] == 0) and np.all(v[z, :, W:] == 0)
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD])
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
 def test_half_storage(ragged, dtype, fetch):
     """Projections stored as FP16/BF16; interpolation and accumulation in
@@ -168,7 +169,7 @@ def fdk128():
     return s, _oracle(s)
 
 
-@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX])
+@pytest.mark.parametrize("fetch", [fdk.FETCH_LDG, fdk.FETCH_TEX, fdk.FETCH_QUAD])
 def test_full_128_cube_496_views(fdk128, fetch):
     """The 128^3 x 496-view, 1248 x 960 workload, whole volume."""
     s, ref = fdk128
