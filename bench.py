@@ -32,7 +32,8 @@ METRIC = ("GUp/s (voxel updates/s) at 512³×496 views, fwd+adjoint; "
 UNIT = "GUp/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-ISSUE_SLOTS_PER_UPDATE = 27      # algorithmic work per update
+ISSUE_SLOTS_PER_UPDATE = 27      # FP32 issue slots per update: 15 FP32 ops, 1 reciprocal, 2 floor, 2 int
+                                 # conversions, 1 address, 2 bounds tests, 4 loads
 PAPER_PHI_GUPS = {"clipped": 8.5, "full": 12.9}   # Xeon Phi 5110P, assembly, 512^3
 
 
