@@ -139,6 +139,44 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
                              const float origin[3], const int32_t det[2],
                              const float *matrices, int32_t n_views, const fdk_opts *opts);
 
+/* Bytes of the fixed staging array behind fdk_backproject_static. */
+#define FDK_STATIC_QUAD_BYTES (64u * 1024u * 1024u)
+
+/*
+ * fdk_backproject_static -- the same back-projection as fdk_backproject,
+ * for callers that must not allocate device memory.  The paper has no
+ * counterpart; this is a service of the library.
+ *
+ * Who needs it: host applications that reserve the GPU's memory for their
+ * own pool at start-up (a cudaMalloc of theirs or ours would then fail or
+ * fragment that pool), reconstruction loops with a fixed memory budget that
+ * forbid allocation once running, and plugins inside frameworks that own
+ * all device memory.  The QUAD and TEX paths of fdk_backproject allocate
+ * their staging buffers on first use; this entry point allocates nothing.
+ *
+ * How: the quad images (see FDK_FETCH_QUAD) are staged in one array of
+ * FDK_STATIC_QUAD_BYTES (64 MiB) compiled into the library; every GPU that
+ * loads the library holds that array until the process exits.  Views are
+ * processed in passes of as many quad images as fit: 16 B per cell of a
+ * (W + 3) x (H + 3) grid for FP32 images, 8 B for FP16/BF16 (a 1248 x 960
+ * FP32 image takes 19.3 MB, three per pass).  A detector whose single quad
+ * image is larger than the array is rejected with FDK_ERR_INVALID_ARG.
+ *
+ * Arguments, layouts and results are those of fdk_backproject; opts->fetch
+ * must be FDK_FETCH_AUTO or FDK_FETCH_QUAD.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array, and each call writes every cell it reads before reading it, so
+ * nothing carries over from an earlier call; calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array and give
+ * undefined results.
+ */
+FDK_API fdk_status fdk_backproject_static(float *volume, const int32_t dims[3],
+                                          const float voxel_size[3], const float origin[3],
+                                          const void *projections, const int32_t det[2],
+                                          const float *matrices, int32_t n_views,
+                                          const fdk_opts *opts);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 FDK_API const char *fdk_last_error(void);
 

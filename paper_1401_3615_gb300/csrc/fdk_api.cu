@@ -468,3 +468,106 @@ fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free back-projection: quad images staged in a fixed array that
+// is part of the library image, for callers that must not allocate.
+namespace fdk {
+
+static __device__ __align__(256) unsigned char g_static_quads[FDK_STATIC_QUAD_BYTES];
+
+static std::mutex g_static_mu;
+static void *g_static_ptr[256] = {};
+
+// Device address of g_static_quads on the current device, looked up once per
+// device with that device current.  (In host code the symbol is only a
+// host-side stand-in; kernels must get this address, never the symbol.)
+static fdk_status static_quads_ptr(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGetDevice failed: %s", cudaGetErrorString(e));
+        return FDK_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 256) return fail(FDK_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_quads);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error("cudaGetSymbolAddress of the static staging array failed: %s",
+                      cudaGetErrorString(e));
+            return FDK_ERR_CUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return FDK_OK;
+}
+
+}  // namespace fdk
+
+extern "C" fdk_status fdk_backproject_static(float *volume, const int32_t dims[3],
+                                             const float voxel_size[3], const float origin[3],
+                                             const void *projections, const int32_t det[2],
+                                             const float *matrices, int32_t n_views,
+                                             const fdk_opts *opts)
+{
+    g_err[0] = 0;
+    const fdk_opts *o = opts ? opts : &kDefaultOpts;
+    fdk_status st = check_opts(o);
+    if (st) return st;
+    if (o->fetch != FDK_FETCH_AUTO && o->fetch != FDK_FETCH_QUAD)
+        return fail(FDK_ERR_INVALID_ARG, "fdk_backproject_static serves FDK_FETCH_AUTO or FDK_FETCH_QUAD only");
+    Geom g;
+    if ((st = check_geometry(dims, voxel_size, origin, det, matrices, n_views, &g))) return st;
+    if (!volume) return fail(FDK_ERR_INVALID_ARG, "volume is null");
+    if (n_views > 0 && !projections) return fail(FDK_ERR_INVALID_ARG, "projections is null");
+    if ((st = check_alignment(volume, 4, "volume"))) return st;
+    if (!quad_supported(g.W, g.H))
+        return fail(FDK_ERR_INVALID_ARG, "detector too large for quad images (2^23 cells)");
+    const size_t qbytes = (size_t)(g.W + 3) * (size_t)(g.H + 3) * quad_elem_size(o->proj_dtype);
+    if (qbytes > (size_t)FDK_STATIC_QUAD_BYTES) {
+        set_error("one quad image needs %zu bytes, more than the %u-byte static staging array",
+                  qbytes, (unsigned)FDK_STATIC_QUAD_BYTES);
+        return FDK_ERR_INVALID_ARG;
+    }
+    if (n_views == 0) return FDK_OK;
+    if ((st = check_alignment(projections, dtype_size(o->proj_dtype), "projections"))) return st;
+    if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
+    if ((st = check_device_ptr(volume, "volume"))) return st;
+    if ((st = check_device_ptr(projections, "projections"))) return st;
+    if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
+    void *scratch = nullptr;
+    if ((st = static_quads_ptr(&scratch))) return st;
+
+    static thread_local BpArgs a;
+    cudaStream_t s = (cudaStream_t)o->stream;
+    const size_t esz = dtype_size(o->proj_dtype);
+    const long long plane = (long long)g.W * g.H;
+    int per = (int)((size_t)FDK_STATIC_QUAD_BYTES / qbytes);
+    if (per > KMAX) per = KMAX;
+    for (int v0 = 0; v0 < n_views; v0 += per) {
+        const int nv = (n_views - v0 < per) ? (n_views - v0) : per;
+        a.g = g;
+        a.vol = volume;
+        a.proj = static_cast<const char *>(projections) + (size_t)v0 * plane * esz;
+        a.plane = plane;
+        a.n_views = nv;
+        a.qpitch = g.W + 3;
+        a.qplane = (long long)(g.W + 3) * (g.H + 3);
+        if (o->matrices_on_device) {
+            a.mats_dev = matrices + (size_t)v0 * 12;
+        } else {
+            a.mats_dev = nullptr;
+            memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
+        }
+        if ((st = launch_make_quads(a.proj, scratch, nv, g.W, g.H, o->proj_dtype, s))) return st;
+        a.quads = scratch;
+        if ((st = launch_backproject(a, FDK_FETCH_QUAD, o->proj_dtype, o->tile, s))) return st;
+    }
+    return FDK_OK;
+}
