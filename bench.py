@@ -183,6 +183,38 @@ def run_reference(args):
     return 0
 
 
+def _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, fwd_ms):
+    """Time the transpose (voxel-driven splat) on the same workload: the
+    volume is read and every view's projection accumulated (+=)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1401_3615_gb300 import fdk
+    out = torch.zeros(proj.shape, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = max(1, min(args.steps, 5))
+    for _ in range(2):
+        fdk.fdk_forwardproject_adjoint(out, vol, mats, vs, org)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fdk.fdk_forwardproject_adjoint(out, vol, mats, vs, org)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    del out
+    return {"value": world * upd_full / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "ratio_to_forward": ms / fwd_ms,
+            "what": "fdk_forwardproject_adjoint (transpose splat) on the same workload"}
+
+
 def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     """End to end through the public API with host buffers: every step copies
     the projections from pinned host memory to the device, back-projects
@@ -283,6 +315,10 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = world * upd_full / (ms_step * 1e-3) / 1e9
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, ms_step)
+
     e2e = None
     if not args.no_e2e:
         e2e = _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full)
@@ -326,6 +362,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "adjoint": adjoint,
             "gpu_launches": args.steps * passes,
             "clocks": clk,
             "clipped_gups": world * upd_clip / (ms_step * 1e-3) / 1e9,
@@ -350,6 +387,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

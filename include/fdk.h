@@ -115,12 +115,16 @@ FDK_API fdk_status fdk_backproject(float *volume, const int32_t dims[3], const f
                            const float *matrices, int32_t n_views, const fdk_opts *opts);
 
 /*
- * fdk_forwardproject_adjoint -- the exact transpose of fdk_backproject:
- * for every view k and voxel, scatter volume[z][y][x] / w^2 onto the four
- * pixels around (u, v) with the bilinear weights, accumulating (+=) into
- * `projections` (FP32 only).  Same geometry arguments and conventions as
- * fdk_backproject; `volume` is read only.  Accumulation uses atomics, so the
- * result is deterministic only up to FP32 summation order.
+ * fdk_forwardproject_adjoint -- the transpose of fdk_backproject (the paper
+ * has only the back-projection, Listing 1; its transpose is what gradient
+ * based reconstruction needs).  For every view k and voxel, with the same
+ * FP32 detector arithmetic as fdk_backproject, volume[z][y][x] / w^2 is
+ * spread over the four pixels around (u, v) with the bilinear weights
+ * (1-a)(1-b), a(1-b), (1-a)b, ab, accumulating (+=) into `projections`
+ * (device, FP32, n_views*H*W); pixels outside the image receive nothing.
+ * Same geometry arguments and conventions as fdk_backproject; `volume` is
+ * read only; opts->proj_dtype must be FDK_F32.  Accumulation uses atomics,
+ * so the result is deterministic only up to FP32 summation order.
  */
 FDK_API fdk_status fdk_forwardproject_adjoint(void *projections, const int32_t det[2],
                                       const float *volume, const int32_t dims[3],

@@ -415,10 +415,43 @@ fdk_status fdk_forwardproject_adjoint(void *projections, const int32_t det[2], c
                                       const float origin[3], const float *matrices,
                                       int32_t n_views, const fdk_opts *opts)
 {
-    (void)projections; (void)det; (void)volume; (void)dims; (void)voxel_size; (void)origin;
-    (void)matrices; (void)n_views; (void)opts;
     g_err[0] = 0;
-    return fail(FDK_ERR_UNSUPPORTED, "adjoint not built yet");
+    const fdk_opts *o = opts ? opts : &kDefaultOpts;
+    fdk_status st = check_opts(o);
+    if (st) return st;
+    if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_INVALID_ARG, "the adjoint writes FP32 projections only");
+    Geom g;
+    if ((st = check_geometry(dims, voxel_size, origin, det, matrices, n_views, &g))) return st;
+    if (!volume) return fail(FDK_ERR_INVALID_ARG, "volume is null");
+    if (n_views > 0 && !projections) return fail(FDK_ERR_INVALID_ARG, "projections is null");
+    if ((st = check_alignment(volume, 4, "volume"))) return st;
+    if (n_views == 0) return FDK_OK;
+    if ((st = check_alignment(projections, 4, "projections"))) return st;
+    if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
+    if ((st = check_device_ptr(volume, "volume"))) return st;
+    if ((st = check_device_ptr(projections, "projections"))) return st;
+    if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
+    static thread_local BpArgs a;
+    cudaStream_t s = (cudaStream_t)o->stream;
+    const long long plane = (long long)g.W * g.H;
+    for (int v0 = 0; v0 < n_views; v0 += KMAX) {
+        const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
+        a.g = g;
+        a.vol = const_cast<float *>(volume);   // read only in the adjoint
+        a.proj = nullptr;
+        a.quads = nullptr;
+        a.plane = plane;
+        a.n_views = nv;
+        if (o->matrices_on_device) {
+            a.mats_dev = matrices + (size_t)v0 * 12;
+        } else {
+            a.mats_dev = nullptr;
+            memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
+        }
+        float *out = static_cast<float *>(projections) + (size_t)v0 * plane;
+        if ((st = launch_adjoint(a, out, s))) return st;
+    }
+    return FDK_OK;
 }
 
 fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float voxel_size[3],

@@ -45,10 +45,13 @@ constexpr unsigned kIndexBits = 0x4B000000u;
 // class << 10.  All threads of the CTA call this; it ends with
 // __syncthreads().  Tables are built in chunks of views so that the shared
 // memory they take stays small and the rest of the SM's L1 holds image data.
+// With bbox != nullptr it also stores, per view, the pixel box that holds
+// every in-image tap of the tile, (i0, j0, width, height), widened by one
+// pixel against FP32 rounding and clipped to the image.
 template <int BX, int BY, int R>
 __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0, int z0,
                                  ViewEntry *tab, unsigned char *cls, unsigned short *act,
-                                 int *n_act)
+                                 int *n_act, int4 *bbox = nullptr)
 {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
@@ -136,6 +139,18 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
             c = kGeneral;
         tab[lv] = e;
         cls[lv] = (unsigned char)c;
+        if (bbox) {
+            int4 bb = make_int4(0, 0, 0, 0);
+            if (c == kInterior || c == kBoundary) {
+                const float Hf = (float)g.H;
+                const int i0 = max(0, (int)floorf(fmaxf(umin, -4.0f)) - 1);
+                const int i1 = min(g.W - 1, (int)floorf(fminf(umax, Wf + 4.0f)) + 2);
+                const int j0 = max(0, (int)floorf(fmaxf(vmin, -4.0f)) - 1);
+                const int j1 = min(g.H - 1, (int)floorf(fminf(vmax, Hf + 4.0f)) + 2);
+                if (i1 >= i0 && j1 >= j0) bb = make_int4(i0, j0, i1 - i0 + 1, j1 - j0 + 1);
+            }
+            bbox[lv] = bb;
+        }
     }
     __syncthreads();
     if (tid < 32) {

@@ -1,0 +1,179 @@
+"""GPU parity of the transpose (fdk_forwardproject_adjoint) and of autograd.
+
+The adjoint is checked elementwise against the FP64 oracle's transpose, by
+the dot-product identity <B y, x> = <y, B^T x>, by central finite
+differences of a loss through the autograd wrapper, and by 20 steps of
+least-squares reconstruction whose loss must fall.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _helpers import assert_parity
+from paper_1401_3615_gb300 import autograd, fdk
+
+pytestmark = pytest.mark.gpu
+NCPU = os.cpu_count() or 1
+
+
+def _gpu_adj(scan, vol):
+    n = scan["mats"].shape[0]
+    cfg = scan["cfg"]
+    proj = torch.zeros((n, cfg.det_h, cfg.det_w), device="cuda")
+    fdk.fdk_forwardproject_adjoint(proj, vol, scan["mats"], scan["voxel_size"], scan["origin"])
+    torch.cuda.synchronize()
+    return proj
+
+
+def _oracle_adj(scan, vol_np, mats=None):
+    cfg = scan["cfg"]
+    m = scan["mats"] if mats is None else mats
+    return oracle.adjoint(vol_np, m, scan["dims"], scan["voxel_size"], scan["origin"],
+                          cfg.det_w, cfg.det_h, threads=NCPU)
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    return synth.make_scan(synth.preset("small", nx=37, ny=29, nz=21), device="cuda")
+
+
+def test_adjoint_parity_ragged(ragged):
+    x = synth.gaussian_volume(ragged["dims"], seed=31)
+    got = _gpu_adj(ragged, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = _oracle_adj(ragged, x)
+    assert_parity(ref, got, what="adjoint")
+
+
+def test_adjoint_accumulates_and_multi_pass():
+    s = synth.make_scan(synth.preset("small", n_views=600, det_w=40, det_h=32, nx=20, ny=18, nz=10),
+                        device="cuda")
+    x = synth.gaussian_volume(s["dims"], seed=32)
+    proj = torch.full((600, 32, 40), 0.25, device="cuda")
+    fdk.fdk_forwardproject_adjoint(proj, torch.from_numpy(x).cuda(), s["mats"], s["voxel_size"],
+                                   s["origin"])
+    torch.cuda.synchronize()
+    ref = _oracle_adj(s, x) + 0.25
+    assert_parity(ref, proj.cpu().numpy())
+
+
+def test_adjoint_source_inside_volume():
+    """The source circle (radius 150 mm) lies within the 400 mm x-y extent
+    of the volume, so tiles straddle the source's principal plane and hold
+    w <= 0 voxels, which receive nothing.  The volume sits 40 mm above the
+    plane of the source circle: a voxel that projects onto the detector is
+    then at least 83 mm deep (w >= 0.55), so no contribution hangs on a voxel
+    a few mm in front of the source, where 1/w^2 would amplify FP32 rounding
+    beyond the accuracy bar."""
+    s = synth.make_scan(synth.preset("small", nx=40, ny=40, nz=8, voxel=10.0, sid=150.0, sdd=300.0),
+                        device="cuda")
+    s["origin"] = s["origin"] + np.float32([0.0, 0.0, 75.0])
+    x = synth.gaussian_volume(s["dims"], seed=33)
+    assert_parity(_oracle_adj(s, x), _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy(),
+                  what="source inside")
+
+
+def test_adjoint_large_footprints():
+    """Coarse voxels on a fine detector: per-view footprints larger than the
+    shared-memory buffer take the direct-atomic path."""
+    big = synth.make_scan(synth.preset("small", nx=24, ny=24, nz=8, voxel=8.0, n_views=6,
+                                       det_w=400, det_h=300, pixel=0.308), device="cuda")
+    xb = synth.gaussian_volume(big["dims"], seed=34)
+    assert_parity(_oracle_adj(big, xb), _gpu_adj(big, torch.from_numpy(xb).cuda()).cpu().numpy(),
+                  what="large footprints")
+
+
+def test_adjoint_full_detector_sampled_views():
+    """256^3 volume, 1248 x 960 detector: 8 of the 248 views of the
+    differentiation workload, whole images, against the oracle."""
+    cfg = synth.PRESETS["fdk256"]
+    geo = synth.geometry(cfg)
+    pick = np.linspace(0, cfg.n_views - 1, 8).astype(int)
+    mats = geo["mats"][pick]
+    dims, vs, org = synth.volume_geometry(cfg)
+    s = {"cfg": cfg, "mats": mats, "dims": dims, "voxel_size": vs, "origin": org}
+    x = synth.gaussian_volume(dims, seed=35)
+    got = _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = _oracle_adj(s, x)
+    assert_parity(ref, got, what="adjoint 256^3")
+
+
+def test_dot_product_identity(ragged):
+    n, H, W = ragged["proj"].shape
+    y = torch.from_numpy(synth.gaussian_projections(n, H, W, seed=41)).cuda()
+    x = torch.from_numpy(synth.gaussian_volume(ragged["dims"], seed=42)).cuda()
+    by = torch.zeros_like(x)
+    fdk.fdk_backproject(by, y, ragged["mats"], ragged["voxel_size"], ragged["origin"])
+    btx = _gpu_adj(ragged, x)
+    lhs = float((by.double() * x.double()).sum())
+    rhs = float((y.double() * btx.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_autograd_gradients_finite_differences(ragged):
+    """d/dy <c, B y> = B^T c checked by central differences (eps = 1e-3) on
+    32 seeded projection pixels; the operator is linear, so the differences
+    are exact up to rounding."""
+    n, H, W = ragged["proj"].shape
+    vol_shape = (int(ragged["dims"][2]), int(ragged["dims"][1]), int(ragged["dims"][0]))
+    c = torch.from_numpy(synth.gaussian_volume(ragged["dims"], seed=43)).cuda().double()
+    y = ragged["proj"].clone().requires_grad_(True)
+    vol = autograd.backproject(y, ragged["mats"], ragged["voxel_size"], ragged["origin"], vol_shape)
+    loss = (vol.double() * c).sum()
+    loss.backward()
+    grad = y.grad.detach().cpu().numpy()
+    rng = np.random.default_rng(44)
+    eps = 1e-3
+    for _ in range(32):
+        k, j, i = rng.integers(0, n), rng.integers(0, H), rng.integers(0, W)
+        vals = []
+        for sgn in (1.0, -1.0):
+            yp = ragged["proj"].clone()
+            yp[k, j, i] += sgn * eps
+            vp = autograd.backproject(yp, ragged["mats"], ragged["voxel_size"], ragged["origin"], vol_shape)
+            vals.append(float((vp.double() * c).sum()))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - grad[k, j, i]) <= 2e-3 * max(1.0, abs(grad[k, j, i])), (fd, grad[k, j, i])
+
+
+def test_autograd_forwardproject_backward_is_backprojection(ragged):
+    n, H, W = ragged["proj"].shape
+    x = torch.from_numpy(synth.gaussian_volume(ragged["dims"], seed=45)).cuda().requires_grad_(True)
+    q = autograd.forwardproject(x, ragged["mats"], ragged["voxel_size"], ragged["origin"], (n, H, W))
+    g = torch.from_numpy(synth.gaussian_projections(n, H, W, seed=46)).cuda()
+    (q * g).sum().backward()
+    expect = torch.zeros_like(x)
+    fdk.fdk_backproject(expect, g, ragged["mats"], ragged["voxel_size"], ragged["origin"])
+    torch.cuda.synchronize()
+    assert_parity(expect.detach().cpu().numpy(), x.grad.cpu().numpy())
+
+
+def test_least_squares_reconstruction_20_steps():
+    """min_x ||B^T x - y||^2 over x by gradient descent with the exact
+    Lipschitz step; the loss falls monotonically over 20 steps."""
+    cfg = synth.preset("small", nx=32, ny=32, nz=16, voxel=6.0, n_views=60, det_w=96, det_h=64,
+                       pixel=0.308 * 13)
+    s = synth.make_scan(cfg, device="cuda", filtered=False)
+    shape = (cfg.nz, cfg.ny, cfg.nx)
+    det = (cfg.n_views, cfg.det_h, cfg.det_w)
+    A = lambda v: autograd.forwardproject(v, s["mats"], s["voxel_size"], s["origin"], det)
+    # Lipschitz constant of the gradient: 2 * largest eigenvalue of B B^T (power iteration)
+    v = torch.randn(shape, device="cuda")
+    for _ in range(30):
+        v = autograd.backproject(A(v), s["mats"], s["voxel_size"], s["origin"], shape)
+        v = v / v.norm()
+    lam = float((A(v) ** 2).sum())
+    y = s["proj"]
+    x = torch.zeros(shape, device="cuda", requires_grad=True)
+    losses = []
+    for _ in range(20):
+        loss = ((A(x) - y) ** 2).sum()
+        losses.append(float(loss.detach()))
+        g, = torch.autograd.grad(loss, x)
+        with torch.no_grad():
+            x -= g / (2.0 * lam)
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(losses, losses[1:])), losses
+    assert losses[-1] < 0.5 * losses[0], losses
