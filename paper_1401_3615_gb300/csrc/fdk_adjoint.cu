@@ -9,28 +9,61 @@
 //
 // Scatter strategy: per (tile, view) the CTA first accumulates into a
 // shared-memory copy of the tile's detector footprint (its corner-derived
-// pixel box) with shared atomics, then adds the non-zero cells to the
-// projections with one global atomic each.  Footprints too large for the
-// shared buffer fall back to direct global atomics.
+// pixel box), then adds the non-zero cells to the projections with one
+// global atomic per cell (one 16-byte vector atomic per 4 cells when rows are
+// aligned).  The shared accumulation is fixed point with native 32-bit
+// integer atomics (an FP32 add on shared memory is a compare-and-swap loop):
+// contributions are scaled by s = (2^31 - 2^13) wmin^2 / sum|f|, with sum|f|
+// over the tile's voxels and wmin the tile's smallest w for the view, so no
+// cell can overflow whatever the geometry, and each contribution is
+// rounded to 1/s, about 1e-6 of a typical contribution.  Footprints too
+// large for the shared buffer fall back to direct FP32 global atomics.
 #include "fdk_tile.cuh"
 
 namespace fdk {
 
 constexpr int kAdjBX = 16, kAdjBY = 16, kAdjR = 8, kAdjChunk = 64;
-constexpr int kAdjCap = 6144;   // floats of shared footprint buffer (24 KB)
+constexpr int kAdjCap = 16384;  // cells of the shared footprint buffer (64 KB, dynamic)
 
-__device__ __forceinline__ void adj_tap(float *acc_s, float *proj, const int4 &bb, int W, int H,
-                                        int ti, int tj, float val)
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// One tap of a boundary or near-source voxel: pixels outside the image get
+// nothing; pixels inside the tile's footprint box go to the shared buffer,
+// any other (never expected) to the projections directly.
+__device__ __forceinline__ void adj_tap_checked(int *acc_s, bool fixed, float scale, float *proj,
+                                                const int4 &bb, bool fits, int W, int H, int ti,
+                                                int tj, float val)
 {
-    if ((unsigned)ti >= (unsigned)W || (unsigned)tj >= (unsigned)H || val == 0.0f) return;
+    if ((unsigned)ti >= (unsigned)W || (unsigned)tj >= (unsigned)H) return;
     const int li = ti - bb.x, lj = tj - bb.y;
-    if ((unsigned)li < (unsigned)bb.z && (unsigned)lj < (unsigned)bb.w && bb.z * bb.w <= kAdjCap)
-        atomicAdd(acc_s + lj * bb.z + li, val);
-    else
+    if (fits && (unsigned)li < (unsigned)bb.z && (unsigned)lj < (unsigned)bb.w) {
+        if (fixed) atomicAdd(acc_s + lj * bb.z + li, __float2int_rn(val * scale));
+        else atomicAdd(reinterpret_cast<float *>(acc_s) + lj * bb.z + li, val);
+    } else {
         atomicAdd(proj + (long long)tj * W + ti, val);
+    }
 }
 
-template <int BX, int BY, int R>
+// The four weighted taps of a voxel: value g = f / w^2 and fractions (a, b).
+struct Taps {
+    float w00, w10, w01, w11;
+};
+__device__ __forceinline__ Taps tap_weights(float g, float a, float b)
+{
+    const float gh = g * b, gl = g - gh;
+    Taps t;
+    t.w10 = gl * a;
+    t.w00 = gl - t.w10;
+    t.w11 = gh * a;
+    t.w01 = gh - t.w11;
+    return t;
+}
+
+// VEC4: rows of the projections are 16-byte aligned (W % 4 == 0 and an
+// aligned base), so footprint boxes are widened to 4-pixel groups and
+// flushed with one vector atomic per group.
+template <int BX, int BY, int R, bool VEC4>
 __global__ void __launch_bounds__(BX * BY, 3)
 fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
 {
@@ -39,11 +72,13 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     __shared__ unsigned char cls[kAdjChunk];
     __shared__ unsigned short act[kAdjChunk];
     __shared__ int4 bbox[kAdjChunk];
+    __shared__ float2 wrange[kAdjChunk];
     __shared__ int n_act;
-    __shared__ float acc_s[kAdjCap];
+    extern __shared__ __align__(16) int acc_s[];   // kAdjCap cells: fixed point, or FP32 bits
+    __shared__ float red_s[NT / 32];
 
     const int tid = threadIdx.x;
-    for (int p = tid; p < kAdjCap; p += NT) acc_s[p] = 0.0f;
+    for (int p = tid; p < kAdjCap; p += NT) acc_s[p] = 0;
 
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * R;
     const int lane = tid & 31, warp = tid >> 5;
@@ -63,51 +98,130 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
         const int z = z0 + r;
         f[r] = (inxy && z < a.g.nz) ? __ldg(a.vol + (long long)z * sxy + (long long)y * a.g.nx + x) : 0.0f;
     }
+    // sum |f| over the tile: bounds every footprint cell's sum
+    float sf = 0.0f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sf += fabsf(f[r]);
+    for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+    if (lane == 0) red_s[warp] = sf;
+    __syncthreads();
+    float ftile = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) ftile += red_s[w];
+    if (!(ftile > 0.0f)) return;   // uniform: an all-zero tile adds nothing
+    ftile *= 1.0009765625f;         // headroom for the FP32 rounding of the sum
 
     for (int v0 = 0; v0 < a.n_views; v0 += kAdjChunk) {
         const int nv = min(kAdjChunk, a.n_views - v0);
-        build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act, bbox);
+        build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act, bbox, wrange);
         const int n = n_act;
         for (int q = 0; q < n; ++q) {
             const int ev = act[q];
             const int lv = ev & 1023, c = ev >> 10;
             const ViewEntry e = tab[lv];
-            const int4 bb = bbox[lv];
-            float *proj = proj_out + (long long)(v0 + lv) * a.plane;
-            const float bu = fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x));
-            const float bv = fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y));
-            const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
-            const int U = (int)e.o.x, V = (int)e.o.y;
-            const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
-            const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float rf = (float)(r - R / 2);
-                const float wl = fmaf(rf, e.w.w, bw);
-                const float iw = rcp_approx(wl);
-                float us = fmaf(rf, e.b.z, bu) * iw, vs = fmaf(rf, e.b.w, bv) * iw;
-                us = fminf(fmaxf(us, lou), hiu);
-                vs = fminf(fmaxf(vs, lov), hiv);
-                const float tu = __fadd_rd(us, kFloorMagic), tv = __fadd_rd(vs, kFloorMagic);
-                const float au = us - (tu - kFloorMagic), bvv = vs - (tv - kFloorMagic);
-                const int i = __float_as_int(tu) - kFloorBits + U;
-                const int j = __float_as_int(tv) - kFloorBits + V;
-                float g = f[r] * iw * iw;
-                if (c == kGeneral && !(wl > 0.0f)) g = 0.0f;
-                const float gl = g * (1.0f - bvv), gh = g * bvv;
-                adj_tap(acc_s, proj, bb, W, H, i, j, gl * (1.0f - au));
-                adj_tap(acc_s, proj, bb, W, H, i + 1, j, gl * au);
-                adj_tap(acc_s, proj, bb, W, H, i, j + 1, gh * (1.0f - au));
-                adj_tap(acc_s, proj, bb, W, H, i + 1, j + 1, gh * au);
+            int4 bb = bbox[lv];
+            if (VEC4 && bb.z > 0) {
+                const int i0 = bb.x & ~3, i1 = ((bb.x + bb.z + 3) & ~3);
+                bb.x = i0;
+                bb.z = i1 - i0;
             }
             const int npx = bb.z * bb.w;
-            if (npx > 0 && npx <= kAdjCap) {
+            const float2 wr = wrange[lv];
+            const bool fits = npx > 0 && npx <= kAdjCap;
+            // fixed point when w varies little over the tile, else FP32 cells
+            const bool fixed = fits && wr.x > 0.0f && wr.y <= 1.5f * wr.x;
+            const float scale = fixed ? 2147475456.0f * (wr.x * wr.x) / ftile : 0.0f;
+            const float inv_scale = fixed ? ftile / (2147475456.0f * (wr.x * wr.x)) : 0.0f;
+            float *proj = proj_out + (long long)(v0 + lv) * a.plane;
+            const float2 buv = __ffma2_rn(f2(dyf), f2(e.b.x, e.b.y), __ffma2_rn(f2(dxf), f2(e.a.z, e.a.w), f2(e.a.x, e.a.y)));
+            const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
+            const float2 gz = f2(e.b.z, e.b.w);
+            const int U = (int)e.o.x, V = (int)e.o.y;
+            if (c == kInterior && fixed) {
+                // every tap is inside the image and, by the 1-pixel margin of
+                // the box, inside the footprint; the clamp only guards memory
+                // index = (j - j0) * bw + (i - i0) with i, j taken from the
+                // floor bits; the bias is folded in modulo 2^32 (unsigned)
+                const unsigned bz = (unsigned)bb.z;
+                const unsigned base = (unsigned)((V - bb.y) * bb.z + (U - bb.x)) -
+                                      ((unsigned)kFloorBits * bz + (unsigned)kFloorBits);
+                const int hi_idx = npx - bb.z - 2;
+#pragma unroll
+                for (int r = 0; r < R; r += 2) {
+                    const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
+                    const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(bw));
+                    const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
+                    const float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, buv), f2(iw0));
+                    const float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, buv), f2(iw1));
+                    const float2 t0 = __fadd2_rd(uv0, f2(kFloorMagic)), t1 = __fadd2_rd(uv1, f2(kFloorMagic));
+                    const float2 ab0 = __fadd2_rn(uv0, __fadd2_rn(f2(kFloorMagic), __fmul2_rn(t0, f2(-1.0f))));
+                    const float2 ab1 = __fadd2_rn(uv1, __fadd2_rn(f2(kFloorMagic), __fmul2_rn(t1, f2(-1.0f))));
+                    const float2 g = __fmul2_rn(f2(f[r], f[r + 1]), __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1)));
+                    const Taps k0 = tap_weights(g.x, ab0.x, ab0.y), k1 = tap_weights(g.y, ab1.x, ab1.y);
+                    int i0 = (int)(__float_as_uint(t0.y) * bz + __float_as_uint(t0.x) + base);
+                    int i1 = (int)(__float_as_uint(t1.y) * bz + __float_as_uint(t1.x) + base);
+                    i0 = min(max(i0, 0), hi_idx);
+                    i1 = min(max(i1, 0), hi_idx);
+                    atomicAdd(acc_s + i0, __float2int_rn(k0.w00 * scale));
+                    atomicAdd(acc_s + i0 + 1, __float2int_rn(k0.w10 * scale));
+                    atomicAdd(acc_s + i0 + bb.z, __float2int_rn(k0.w01 * scale));
+                    atomicAdd(acc_s + i0 + bb.z + 1, __float2int_rn(k0.w11 * scale));
+                    atomicAdd(acc_s + i1, __float2int_rn(k1.w00 * scale));
+                    atomicAdd(acc_s + i1 + 1, __float2int_rn(k1.w10 * scale));
+                    atomicAdd(acc_s + i1 + bb.z, __float2int_rn(k1.w01 * scale));
+                    atomicAdd(acc_s + i1 + bb.z + 1, __float2int_rn(k1.w11 * scale));
+                }
+            } else {
+                const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
+                const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float rf = (float)(r - R / 2);
+                    const float wl = fmaf(rf, e.w.w, bw);
+                    const float iw = rcp_approx(wl);
+                    float2 uv = __fmul2_rn(__ffma2_rn(f2(rf), gz, buv), f2(iw));
+                    uv = f2(fminf(fmaxf(uv.x, lou), hiu), fminf(fmaxf(uv.y, lov), hiv));
+                    const float2 t = __fadd2_rd(uv, f2(kFloorMagic));
+                    const float au = uv.x - (t.x - kFloorMagic), bv = uv.y - (t.y - kFloorMagic);
+                    const int i = __float_as_int(t.x) - kFloorBits + U;
+                    const int j = __float_as_int(t.y) - kFloorBits + V;
+                    float g = f[r] * iw * iw;
+                    if (c == kGeneral && !(wl > 0.0f)) g = 0.0f;
+                    if (g == 0.0f) continue;
+                    const Taps k = tap_weights(g, au, bv);
+                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i, j, k.w00);
+                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i + 1, j, k.w10);
+                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i, j + 1, k.w01);
+                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
+                }
+            }
+            if (fits) {
                 __syncthreads();
-                for (int p = tid; p < npx; p += NT) {
-                    const float s = acc_s[p];
-                    if (s != 0.0f) {
-                        atomicAdd(proj + (long long)(bb.y + p / bb.z) * W + bb.x + p % bb.z, s);
-                        acc_s[p] = 0.0f;
+                // cells hold fixed point (scaled ints) or FP32 bits; both are
+                // zero when untouched and are reset to zero after the flush
+                if (VEC4) {
+                    const int gw = bb.z >> 2;
+                    int4 *acc4 = reinterpret_cast<int4 *>(acc_s);
+                    for (int p = tid; p < (npx >> 2); p += NT) {
+                        const int4 s4 = acc4[p];
+                        if ((s4.x | s4.y | s4.z | s4.w) != 0) {
+                            const int row = p / gw, col = (p - row * gw) << 2;
+                            const float4 v = fixed
+                                ? make_float4((float)s4.x * inv_scale, (float)s4.y * inv_scale,
+                                              (float)s4.z * inv_scale, (float)s4.w * inv_scale)
+                                : make_float4(__int_as_float(s4.x), __int_as_float(s4.y),
+                                              __int_as_float(s4.z), __int_as_float(s4.w));
+                            atomicAdd(reinterpret_cast<float4 *>(proj + (long long)(bb.y + row) * W + bb.x + col), v);
+                            acc4[p] = make_int4(0, 0, 0, 0);
+                        }
+                    }
+                } else {
+                    for (int p = tid; p < npx; p += NT) {
+                        const int s1 = acc_s[p];
+                        if (s1 != 0) {
+                            const float v = fixed ? (float)s1 * inv_scale : __int_as_float(s1);
+                            atomicAdd(proj + (long long)(bb.y + p / bb.z) * W + bb.x + p % bb.z, v);
+                            acc_s[p] = 0;
+                        }
                     }
                 }
                 __syncthreads();
@@ -120,8 +234,18 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
 fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t s)
 {
     dim3 grid((a.g.nx + kAdjBX - 1) / kAdjBX, (a.g.ny + kAdjBY - 1) / kAdjBY, (a.g.nz + kAdjR - 1) / kAdjR);
-    fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR><<<grid, kAdjBX * kAdjBY, 0, s>>>(a, proj_out);
-    cudaError_t err = cudaGetLastError();
+    const bool vec4 = (a.g.W % 4) == 0 && ((uintptr_t)proj_out % 16) == 0;
+    const size_t smem = (size_t)kAdjCap * sizeof(int);
+    auto k = vec4 ? fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, true> : fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, false>;
+    // opt in to more than 48 KB of dynamic shared memory (idempotent)
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        set_error("adjoint: shared-memory opt-in failed: %s", cudaGetErrorString(err));
+        return FDK_ERR_CUDA;
+    }
+    k<<<grid, kAdjBX * kAdjBY, smem, s>>>(a, proj_out);
+    err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error("adjoint launch failed: %s", cudaGetErrorString(err));
         return FDK_ERR_CUDA;

@@ -47,11 +47,13 @@ constexpr unsigned kIndexBits = 0x4B000000u;
 // memory they take stays small and the rest of the SM's L1 holds image data.
 // With bbox != nullptr it also stores, per view, the pixel box that holds
 // every in-image tap of the tile, (i0, j0, width, height), widened by one
-// pixel against FP32 rounding and clipped to the image.
+// pixel against FP32 rounding and clipped to the image, and in wrange the
+// smallest and largest w of the tile's corners (of the whole tile, since w
+// is linear in the voxel position).
 template <int BX, int BY, int R>
 __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0, int z0,
                                  ViewEntry *tab, unsigned char *cls, unsigned short *act,
-                                 int *n_act, int4 *bbox = nullptr)
+                                 int *n_act, int4 *bbox = nullptr, float2 *wrange = nullptr)
 {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
@@ -101,6 +103,7 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
 
         // classify from the 8 corners
         float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+        float wlo = 3.0e38f, whi = -3.0e38f;
         int npos = 0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -110,6 +113,8 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
             const float wl = fmaf(dz, e.w.w, fmaf(dy, e.w.z, fmaf(dx, e.w.y, e.w.x)));
             const float ul = fmaf(dz, e.b.z, fmaf(dy, e.b.x, fmaf(dx, e.a.z, e.a.x)));
             const float vl = fmaf(dz, e.b.w, fmaf(dy, e.b.y, fmaf(dx, e.a.w, e.a.y)));
+            wlo = fminf(wlo, wl);
+            whi = fmaxf(whi, wl);
             if (wl > 0.0f) {
                 ++npos;
                 const float r = rcp_approx(wl);
@@ -150,6 +155,7 @@ __device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0
                 if (i1 >= i0 && j1 >= j0) bb = make_int4(i0, j0, i1 - i0 + 1, j1 - j0 + 1);
             }
             bbox[lv] = bb;
+            wrange[lv] = make_float2(wlo, whi);
         }
     }
     __syncthreads();
