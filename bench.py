@@ -35,6 +35,21 @@ FP32_LANES_PER_SM = 128
 ISSUE_SLOTS_PER_UPDATE = 27      # FP32 issue slots per update: 15 FP32 ops, 1 reciprocal, 2 floor, 2 int
                                  # conversions, 1 address, 2 bounds tests, 4 loads
 PAPER_PHI_GUPS = {"clipped": 8.5, "full": 12.9}   # Xeon Phi 5110P, assembly, 512^3
+# DRAM bytes (read + write) of one full-size back-projection launch from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
+# the kernel sources hash to the value they were taken with.
+KERNEL_SOURCES = ["paper_1401_3615_gb300/csrc/fdk_bp_kernel.cuh", "paper_1401_3615_gb300/csrc/fdk_tile.cuh",
+                  "paper_1401_3615_gb300/csrc/fdk_internal.cuh", "paper_1401_3615_gb300/csrc/fdk_bp_ldg32.cu"]
+MEASURED_TRAFFIC = {("fdk512", 496, 0, 0): {"bytes": 19.28e9 + 0.558e9, "sources": "16788905c3c96344"}}
+
+
+def _sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -330,8 +345,11 @@ def run_ours(args):
         peak_gups = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / ISSUE_SLOTS_PER_UPDATE / 1e9
         mean_launch = float(np.mean(launch_ms))
         achieved = upd_clip / passes / (mean_launch * 1e-3) / 1e9
+        tr = MEASURED_TRAFFIC.get((args.config, cfg.n_views, args.fetch, args.tile))
+        traffic = tr["bytes"] if tr and tr["sources"] == _sources_sha() else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                    "frac": achieved / peak_gups, "traffic": None,
+                    "frac": achieved / peak_gups, "traffic": traffic,
+                    "traffic_unit": "bytes per launch (ncu dram read + write)",
                     "peak_basis": (f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
                                    f"/ {ISSUE_SLOTS_PER_UPDATE} issue slots per update"),
                     "achieved_basis": f"clipped updates {upd_clip:.4e} / mean launch time",
