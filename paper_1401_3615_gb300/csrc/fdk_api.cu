@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <math.h>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -377,16 +378,9 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         a.vol = volume;
         a.proj = static_cast<const char *>(projections) + (size_t)v0 * plane * esz;
         a.plane = plane;
-        a.n_views = nv;
         a.quads = nullptr;
         a.qpitch = g.W + 3;
         a.qplane = (long long)(g.W + 3) * (g.H + 3);
-        if (o->matrices_on_device) {
-            a.mats_dev = matrices + (size_t)v0 * 12;
-        } else {
-            a.mats_dev = nullptr;
-            memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
-        }
         if (use_tex) {
             for (int k = 0; k < nv; ++k) {
                 const char *src = static_cast<const char *>(a.proj) + (size_t)k * plane * esz;
@@ -404,7 +398,38 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
             if ((st = launch_make_quads(a.proj, qstage->buf, nv, g.W, g.H, o->proj_dtype, s))) return st;
             a.quads = qstage->buf;
         }
-        if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
+        if (o->matrices_on_device || use_tex) {
+            // one launch over the pass in view order with 8 x 4 warp patches
+            a.n_views = nv;
+            a.warp_x = 8;
+            for (int k = 0; k < nv; ++k) a.vidx[k] = k;
+            if (o->matrices_on_device) {
+                a.mats_dev = matrices + (size_t)v0 * 12;
+            } else {
+                a.mats_dev = nullptr;
+                memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
+            }
+            if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
+            continue;
+        }
+        // host matrices: one launch per ray orientation, each with the warp
+        // patch that touches the fewest L1 banks for its views (rays mostly
+        // along x: 4 x 8; along y: 8 x 4); each voxel still sums every view
+        a.mats_dev = nullptr;
+        for (int group = 0; group < 2; ++group) {
+            int cnt = 0;
+            for (int k = 0; k < nv; ++k) {
+                const float *P = matrices + (size_t)(v0 + k) * 12;
+                const bool along_x = fabsf(P[8]) > fabsf(P[9]);
+                if (along_x != (group == 0)) continue;
+                memcpy(a.mats + 12 * cnt, P, sizeof(float) * 12);
+                a.vidx[cnt++] = k;
+            }
+            if (cnt == 0) continue;
+            a.n_views = cnt;
+            a.warp_x = group == 0 ? 4 : 8;
+            if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
+        }
     }
     if (guard) cudaEventRecord(guard, s);
     return FDK_OK;
@@ -600,6 +625,8 @@ extern "C" fdk_status fdk_backproject_static(float *volume, const int32_t dims[3
         }
         if ((st = launch_make_quads(a.proj, scratch, nv, g.W, g.H, o->proj_dtype, s))) return st;
         a.quads = scratch;
+        a.warp_x = 8;
+        for (int k = 0; k < nv; ++k) a.vidx[k] = k;
         if ((st = launch_backproject(a, FDK_FETCH_QUAD, o->proj_dtype, o->tile, s))) return st;
     }
     return FDK_OK;

@@ -350,11 +350,11 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
                 else view_tex<R, T, true>(acc, e, dxf, dyf, tex, W, H);
             } else if (FETCH == kQuad && c != kGeneral) {
                 const void *qimg = static_cast<const char *>(a.quads) +
-                                   (long long)v * a.qplane * (long long)sizeof(typename QuadType<T>::type);
+                                   (long long)a.vidx[v] * a.qplane * (long long)sizeof(typename QuadType<T>::type);
                 if (c == kInterior) view_quad<R, T, false>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
                 else view_quad<R, T, true>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
             } else {
-                const T *img = proj + (long long)v * a.plane;
+                const T *img = proj + (long long)a.vidx[v] * a.plane;
                 if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
                 else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
                 else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
@@ -376,9 +376,9 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
 }
 
 // CTA tile variants (BX x BY voxels in x, y; R voxels per thread along z;
-// minimum resident CTAs per SM for the register budget).  Warps always
-// cover 8 x 4 voxel patches, the shape with the fewest distinct cache lines
-// per gather.  Index 0 is the default (the fastest at 512^3 x 496 views,
+// minimum resident CTAs per SM for the register budget).  Warps cover 8 x 4
+// or 4 x 8 voxel patches (BpArgs::warp_x): views whose rays run mostly along
+// x project a 4 x 8 patch onto fewer L1 banks, views along y an 8 x 4 patch.  Index 0 is the default (the fastest at 512^3 x 496 views,
 // 1248 x 960) and shares its kernel with index 1.
 struct TileCfg { int bx, by, r, minb; };
 constexpr int kNumTiles = 8;
@@ -392,7 +392,10 @@ fdk_status launch_one(const BpArgs &a, cudaStream_t s)
 {
     constexpr int KCHUNK = 128;
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + R - 1) / R);
-    fdk_bp_kernel<BX, BY, 8, R, MINB, KCHUNK, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
+    if (a.warp_x == 4)
+        fdk_bp_kernel<BX, BY, 4, R, MINB, KCHUNK, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
+    else
+        fdk_bp_kernel<BX, BY, 8, R, MINB, KCHUNK, FETCH, T, FIDX><<<grid, BX * BY, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error("back-projection launch failed: %s", cudaGetErrorString(err));

@@ -33,9 +33,11 @@ struct BpArgs {
     int qpitch;                // quad cells per quad-image row: W + 3
     long long qplane;          // quad cells per quad image: (W + 3) * (H + 3)
     long long plane;           // W*H elements per image
-    int n_views;               // views in this pass (<= KMAX)
+    int n_views;               // views in this launch (<= KMAX)
+    int warp_x;                // voxels along x per warp patch: 8 (8x4) or 4 (4x8)
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
     unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
+    int vidx[KMAX];            // image index (within the pass's images) of each view
 };
 
 // Per (tile, view) entry computed in each CTA's prologue (shared memory).
