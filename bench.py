@@ -198,6 +198,52 @@ def run_reference(args):
     return 0
 
 
+def _precision_report(args, cfg, scan, proj, proj32, vol, mats, vs, org):
+    """Error of the low-precision-storage result, reported per result: against
+    the FP32-storage GPU result on the whole volume, and against the FP64
+    oracle (given the stored values and the FP32 values) on a seeded 64^3
+    sub-block."""
+    import torch
+    import oracle
+    from paper_1401_3615_gb300 import fdk
+    low = torch.zeros_like(vol)
+    fdk.fdk_backproject(low, proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
+    ref = torch.zeros_like(vol)
+    fdk.fdk_backproject(ref, proj32, mats, vs, org, fetch=args.fetch, tile=args.tile)
+    torch.cuda.synchronize()
+    peak = float(ref.abs().max())
+    diff = (low.double() - ref.double())
+    out = {"storage": args.proj_dtype,
+           "vs_fp32_storage_gpu": {"max_abs_over_peak": float(diff.abs().max()) / peak,
+                                   "psnr_db": float(10 * np.log10(peak ** 2 / float((diff ** 2).mean())))}}
+    del diff
+    rng = np.random.default_rng(1024)
+    n0 = rng.integers(0, np.array([cfg.nx, cfg.ny, cfg.nz]) - 64 + 1)
+    # keep the block inside the middle 5/8 of the volume, where the phantom is
+    lo = (np.array([cfg.nx, cfg.ny, cfg.nz]) * 5) // 16
+    n0 = np.minimum(np.maximum(n0, lo), np.array([cfg.nx, cfg.ny, cfg.nz]) - lo - 64)
+    zz, yy, xx = np.meshgrid(*(np.arange(n0[a], n0[a] + 64) for a in (2, 1, 0)), indexing="ij")
+    xyz = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)
+    threads = os.cpu_count() or 1
+    import concurrent.futures as cf
+    chunks = np.array_split(np.arange(len(xyz)), threads)
+
+    def orc(p):
+        with cf.ThreadPoolExecutor(threads) as ex:
+            return np.concatenate(list(ex.map(lambda idx: oracle.backproject_voxels(
+                p, mats, vs, org, xyz[idx]), chunks)))
+    stored = proj.float().cpu().numpy()
+    exact = proj32.cpu().numpy()
+    o_stored, o_exact = orc(stored), orc(exact)
+    g = low[xyz[:, 2], xyz[:, 1], xyz[:, 0]].cpu().numpy().astype(np.float64)
+    pk = float(np.abs(o_exact).max())
+    out["subblock_64"] = {"origin_voxel": [int(v) for v in n0],
+                          "gpu_vs_oracle_same_stored_values": float(np.abs(g - o_stored).max()) / pk,
+                          "gpu_vs_oracle_fp32_values": float(np.abs(g - o_exact).max()) / pk,
+                          "storage_rounding_alone": float(np.abs(o_stored - o_exact).max()) / pk}
+    return out
+
+
 def _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, fwd_ms):
     """Time the transpose (voxel-driven splat) on the same workload: the
     volume is read and every view's projection accumulated (+=)."""
@@ -286,6 +332,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     scan = synth.make_scan(cfg, device=dev)
     proj, mats = scan["proj"], scan["mats"]
+    proj32 = None
+    if args.proj_dtype != "f32":
+        # storage-precision form: the same filtered projections stored as
+        # BF16/FP16; interpolation and accumulation stay FP32
+        proj32 = proj
+        proj = proj32.to(torch.bfloat16 if args.proj_dtype == "bf16" else torch.float16)
     dims, vs, org = scan["dims"], scan["voxel_size"], scan["origin"]
     vol = torch.zeros((cfg.nz, cfg.ny, cfg.nx), dtype=torch.float32, device=dev)
     upd_full = cfg.updates
@@ -339,8 +391,12 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = world * upd_full / (ms_step * 1e-3) / 1e9
 
+    precision = None
+    if proj32 is not None:
+        precision = _precision_report(args, cfg, scan, proj, proj32, vol, mats, vs, org)
+
     adjoint = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and proj32 is None:
         adjoint = _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, ms_step)
 
     e2e = None
@@ -371,7 +427,7 @@ def run_ours(args):
             import oracle
             oracle.build()
             threads = os.cpu_count() or 1
-            rate, desc, _ = _cpu_sample(cfg, proj.cpu().numpy(), mats, dims, vs, org,
+            rate, desc, _ = _cpu_sample(cfg, proj.float().cpu().numpy(), mats, dims, vs, org,
                                         args.cpu_seconds, threads)
             cpu = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                    "sample": desc}
@@ -381,7 +437,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": (f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} FP32 volume "
                                     f"({cfg.voxel} mm), {cfg.n_views} views of {cfg.det_w}x{cfg.det_h} "
-                                    "FP32 filtered projections, 200-degree short scan"),
+                                    f"{args.proj_dtype.upper()} filtered projections, 200-degree short scan"),
                        "updates_per_step": upd_full, "clipped_updates_per_step": upd_clip,
                        "l2": (f"inputs larger than L2 (projections {proj.numel() * proj.element_size() / 1e9:.2f} GB, "
                               f"volume {vol.numel() * 4 / 2**20:.0f} MiB)"),
@@ -391,6 +447,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "adjoint": adjoint,
+            "precision": precision,
             "gpu_launches": args.steps * passes,
             "clocks": clk,
             "clipped_gups": world * upd_clip / (ms_step * 1e-3) / 1e9,
@@ -417,6 +474,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
+    ap.add_argument("--proj-dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="projection storage type (the storage-precision form)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

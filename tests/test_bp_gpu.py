@@ -214,3 +214,32 @@ def test_sampled_512_cube_496_views():
     assert np.all(np.isfinite(g))
     assert err <= 1e-4 * peak, f"max|diff| {err:.3e} > 1e-4 * {peak:.3e}"
     print(f"fdk512 sampled ({len(xyz)} voxels): max|diff|/peak = {err / peak:.3e}")
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_precision_form_1024_subblock(dtype):
+    """The storage-precision workload: 1024^3 FP32 volume, 496 views of
+    1248 x 960 stored as BF16 / FP16.  A seeded 64^3 sub-block is checked
+    against the oracle given the same stored values (the bar applies to the
+    arithmetic; the storage rounding itself is reported by the benchmark)."""
+    cfg = synth.PRESETS["fdk1024"]
+    s = synth.make_scan(cfg, device="cuda")
+    p16 = s["proj"].to(dtype)
+    del s["proj"]
+    vol = torch.zeros((cfg.nz, cfg.ny, cfg.nx), device="cuda")
+    fdk.fdk_backproject(vol, p16, s["mats"], s["voxel_size"], s["origin"])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(64)
+    n0 = rng.integers(0, np.array([cfg.nx, cfg.ny, cfg.nz]) - 64 + 1)
+    # keep the block where the phantom is (the peak is inside the field of view)
+    n0 = np.clip(n0, 320, 640)
+    zz, yy, xx = np.meshgrid(*(np.arange(n0[a], n0[a] + 64) for a in (2, 1, 0)), indexing="ij")
+    xyz = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)
+    stored = p16.float().cpu().numpy()
+    import concurrent.futures as cf
+    chunks = np.array_split(np.arange(len(xyz)), NCPU)
+    with cf.ThreadPoolExecutor(NCPU) as ex:
+        ref = np.concatenate(list(ex.map(lambda idx: oracle.backproject_voxels(
+            stored, s["mats"], s["voxel_size"], s["origin"], xyz[idx]), chunks)))
+    got = vol[xyz[:, 2], xyz[:, 1], xyz[:, 0]].cpu().numpy()
+    assert_parity(ref, got, what=f"1024^3 {dtype} sub-block")
