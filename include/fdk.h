@@ -89,7 +89,9 @@ typedef struct fdk_opts {
                                     0: default (currently 16x16, 8)
                                     1: 16x16, 8   2: 32x16, 4   3: 32x16, 8   4: 32x8, 4
                                     5: 16x16, 4   6: 32x8, 16   7: 16x16, 16 */
-    int32_t reserved[10];        /* must be zero */
+    int32_t autotune;            /* fdk_batch_plan_create only: 1 = time the tile variants on
+                                    the batch and keep the fastest; elsewhere must be 0 */
+    int32_t reserved[9];         /* must be zero */
 } fdk_opts;
 
 /*
@@ -180,6 +182,60 @@ FDK_API fdk_status fdk_backproject_static(float *volume, const int32_t dims[3],
                                           const void *projections, const int32_t det[2],
                                           const float *matrices, int32_t n_views,
                                           const fdk_opts *opts);
+
+/* One scan of a batch: the arguments of one fdk_backproject call (FP32
+ * projections, host matrices). */
+typedef struct fdk_scan {
+    float *volume;               /* device, nz*ny*nx FP32, accumulated (+=) */
+    int32_t dims[3];             /* nx, ny, nz */
+    float voxel_size[3];
+    float origin[3];
+    const float *projections;    /* device, n_views*H*W FP32 */
+    int32_t det[2];              /* W, H */
+    const float *matrices;       /* host, n_views*12 FP32, row-major 3x4 */
+    int32_t n_views;
+} fdk_scan;
+
+/* Opaque plan for back-projecting a fixed set of scans (the batched form). */
+typedef struct fdk_batch_plan_t *fdk_batch_plan;
+
+/*
+ * fdk_batch_plan_create -- prepare the back-projection of n_scans scans of
+ * uneven volume, view and detector size as one persistent launch.  Each
+ * scan is exactly one fdk_backproject call (Listing 1, Sec. IV); the batch
+ * only changes how the work is scheduled.  The plan copies the scans'
+ * descriptors, matrices and a (scan, tile) work list to device memory it
+ * owns (synchronously, on the current device) and keeps the scans' device
+ * pointers: the volumes and projections must stay allocated while the plan
+ * is used.  With opts->autotune = 1 it times the tile variants 0 and 2..5
+ * on the batch (writing into a scratch volume, never into the scans'
+ * volumes) and keeps the fastest; otherwise opts->tile (0..5) is used.
+ * opts->proj_dtype must be FDK_F32 and opts->fetch AUTO or LDG.
+ */
+FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans,
+                                         int32_t n_scans, const fdk_opts *opts);
+
+/*
+ * fdk_batch_plan_execute -- enqueue the batch on `stream` (cudaStream_t,
+ * NULL = legacy default stream): a reset of the plan's work counter and one
+ * persistent kernel in which CTAs take (scan, tile) items from that counter
+ * until none are left.  Every volume is accumulated (+=) exactly as by
+ * fdk_backproject with the plan's tile variant, bit for bit.  It allocates
+ * nothing and does not synchronise.  Executions of one plan must not
+ * overlap on the GPU (they share the counter); the plan's device must be
+ * current.
+ */
+FDK_API fdk_status fdk_batch_plan_execute(fdk_batch_plan plan, void *stream);
+
+/* The tile variant a plan uses (the autotuner's pick when it ran). */
+FDK_API fdk_status fdk_batch_plan_tile(fdk_batch_plan plan, int32_t *tile);
+
+/* Free a plan's device memory.  No execution of it may still be in flight. */
+FDK_API void fdk_batch_plan_destroy(fdk_batch_plan plan);
+
+/* Create, execute on opts->stream, synchronise that stream, destroy. */
+FDK_API fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scans,
+                                           const fdk_opts *opts);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 FDK_API const char *fdk_last_error(void);

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <math.h>
+#include <algorithm>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -29,7 +30,7 @@ static fdk_status fail(fdk_status st, const char *msg)
     return st;
 }
 
-static const fdk_opts kDefaultOpts = {FDK_F32, 0, nullptr, FDK_FETCH_AUTO, 0, {0}};
+static const fdk_opts kDefaultOpts = {FDK_F32, 0, nullptr, FDK_FETCH_AUTO, 0, 0, {0}};
 
 // Shared checks for the geometry arguments of every entry point.
 static fdk_status check_geometry(const int32_t dims[3], const float voxel_size[3],
@@ -70,7 +71,8 @@ static fdk_status check_opts(const fdk_opts *o)
     if (o->fetch < FDK_FETCH_AUTO || o->fetch > FDK_FETCH_QUAD)
         return fail(FDK_ERR_INVALID_ARG, "unknown fetch path");
     if (o->tile < 0 || o->tile > 7) return fail(FDK_ERR_INVALID_ARG, "tile must be 0..7");
-    for (int q = 0; q < 10; ++q)
+    if (o->autotune != 0 && o->autotune != 1) return fail(FDK_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    for (int q = 0; q < 9; ++q)
         if (o->reserved[q] != 0) return fail(FDK_ERR_INVALID_ARG, "reserved option fields must be zero");
     return FDK_OK;
 }
@@ -323,6 +325,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     const fdk_opts *o = opts ? opts : &kDefaultOpts;
     fdk_status st = check_opts(o);
     if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
     // ~29 KB of kernel parameters, filled per pass; one copy per host thread
     static thread_local BpArgs a;
     Geom g;
@@ -444,6 +447,7 @@ fdk_status fdk_forwardproject_adjoint(void *projections, const int32_t det[2], c
     const fdk_opts *o = opts ? opts : &kDefaultOpts;
     fdk_status st = check_opts(o);
     if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
     if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_INVALID_ARG, "the adjoint writes FP32 projections only");
     Geom g;
     if ((st = check_geometry(dims, voxel_size, origin, det, matrices, n_views, &g))) return st;
@@ -487,6 +491,7 @@ fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float 
     const fdk_opts *o = opts ? opts : &kDefaultOpts;
     fdk_status st = check_opts(o);
     if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
     if (!count) return fail(FDK_ERR_INVALID_ARG, "count is null");
     *count = 0;
     Geom g;
@@ -578,6 +583,7 @@ extern "C" fdk_status fdk_backproject_static(float *volume, const int32_t dims[3
     const fdk_opts *o = opts ? opts : &kDefaultOpts;
     fdk_status st = check_opts(o);
     if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
     if (o->fetch != FDK_FETCH_AUTO && o->fetch != FDK_FETCH_QUAD)
         return fail(FDK_ERR_INVALID_ARG, "fdk_backproject_static serves FDK_FETCH_AUTO or FDK_FETCH_QUAD only");
     Geom g;
@@ -631,3 +637,263 @@ extern "C" fdk_status fdk_backproject_static(float *volume, const int32_t dims[3
     }
     return FDK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched back-projection plans.
+struct fdk_batch_plan_t {
+    int dev = 0;
+    int n_scans = 0;
+    int tile = 0;
+    bool fidx = true;
+    int total = 0;
+    void *buf = nullptr;             // descriptors | tile_start | counter | matrices | view indices
+    fdk::ScanDesc *d_descs = nullptr;
+    int *d_tile_start = nullptr;
+    int *d_counter = nullptr;
+    std::vector<fdk::ScanDesc> h_descs;
+};
+
+namespace fdk {
+
+// Work-list prefix counts for a tile variant; returns the item total.
+static int plan_tile_start(const fdk_batch_plan_t *p, int tile, std::vector<int> &ts)
+{
+    int bx, by, r;
+    batched_tile_dims(tile, &bx, &by, &r);
+    ts.assign(p->n_scans + 1, 0);
+    long long acc = 0;
+    for (int s = 0; s < p->n_scans; ++s) {
+        ts[s] = (int)acc;
+        const Geom &g = p->h_descs[2 * s].g;
+        const bool any = p->h_descs[2 * s].n_views + p->h_descs[2 * s + 1].n_views > 0;
+        if (any) acc += (long long)((g.nx + bx - 1) / bx) * ((g.ny + by - 1) / by) * ((g.nz + r - 1) / r);
+    }
+    ts[p->n_scans] = (int)acc;
+    return acc > INT32_MAX ? -1 : (int)acc;
+}
+
+static fdk_status plan_set_tile(fdk_batch_plan_t *p, int tile)
+{
+    std::vector<int> ts;
+    const int total = plan_tile_start(p, tile, ts);
+    if (total < 0) return fail(FDK_ERR_INVALID_ARG, "batch has more than 2^31 work items");
+    if (cudaMemcpy(p->d_tile_start, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "batch plan: upload of the work list failed");
+    }
+    p->tile = tile;
+    p->total = total;
+    return FDK_OK;
+}
+
+static fdk_status plan_launch(fdk_batch_plan_t *p, cudaStream_t s)
+{
+    if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "batch: counter reset failed");
+    }
+    BatchLaunch b;
+    b.descs = p->d_descs;
+    b.tile_start = p->d_tile_start;
+    b.counter = p->d_counter;
+    b.n_scans = p->n_scans;
+    b.total = p->total;
+    return launch_batched(b, p->tile, p->fidx, s);
+}
+
+// Time the tile variants on the batch with every volume redirected to one
+// scratch buffer (the scans' volumes are never written), keep the fastest.
+static fdk_status plan_autotune(fdk_batch_plan_t *p)
+{
+    size_t vmax = 0;
+    for (int s = 0; s < p->n_scans; ++s) {
+        const Geom &g = p->h_descs[2 * s].g;
+        vmax = std::max(vmax, (size_t)g.nx * g.ny * g.nz * sizeof(float));
+    }
+    float *scratch = nullptr;
+    if (cudaMalloc(&scratch, vmax) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_OOM, "autotune: scratch volume allocation failed");
+    }
+    std::vector<ScanDesc> tuned = p->h_descs;
+    for (auto &d : tuned) d.vol = scratch;
+    cudaMemcpy(p->d_descs, tuned.data(), sizeof(ScanDesc) * tuned.size(), cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cands[] = {0, 2, 3, 4, 5};
+    int best = 0;
+    float best_ms = 3.0e38f;
+    fdk_status st = FDK_OK;
+    for (int c : cands) {
+        if ((st = plan_set_tile(p, c))) break;
+        if ((st = plan_launch(p, 0))) break;            // warm-up
+        cudaEventRecord(e0, 0);
+        for (int rep = 0; rep < 2 && st == FDK_OK; ++rep) st = plan_launch(p, 0);
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = fail(FDK_ERR_CUDA, "autotune: timing failed"); }
+        if (st) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemcpy(p->d_descs, p->h_descs.data(), sizeof(ScanDesc) * p->h_descs.size(), cudaMemcpyHostToDevice);
+    cudaDeviceSynchronize();
+    cudaFree(scratch);
+    if (st) return st;
+    return plan_set_tile(p, best);
+}
+
+}  // namespace fdk
+
+extern "C" {
+
+fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, int32_t n_scans,
+                                 const fdk_opts *opts)
+{
+    g_err[0] = 0;
+    if (!plan) return fail(FDK_ERR_INVALID_ARG, "plan is null");
+    *plan = nullptr;
+    fdk_opts o = opts ? *opts : kDefaultOpts;
+    const int autotune = o.autotune;
+    o.autotune = 0;
+    fdk_status st = check_opts(&o);
+    if (st) return st;
+    if (autotune != 0 && autotune != 1) return fail(FDK_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o.proj_dtype != FDK_F32) return fail(FDK_ERR_INVALID_ARG, "batches take FP32 projections");
+    if (o.fetch != FDK_FETCH_AUTO && o.fetch != FDK_FETCH_LDG)
+        return fail(FDK_ERR_INVALID_ARG, "batches use the LDG fetch path");
+    if (o.matrices_on_device) return fail(FDK_ERR_INVALID_ARG, "batches take host matrices");
+    if (o.tile > 5) return fail(FDK_ERR_INVALID_ARG, "batches take tile variants 0..5");
+    if (n_scans < 1 || !scans) return fail(FDK_ERR_INVALID_ARG, "need at least one scan");
+    std::unique_ptr<fdk_batch_plan_t> p(new fdk_batch_plan_t());
+    cudaGetDevice(&p->dev);
+    p->n_scans = n_scans;
+    p->h_descs.resize(2 * (size_t)n_scans);
+    size_t total_views = 0;
+    for (int s = 0; s < n_scans; ++s) {
+        const fdk_scan &sc = scans[s];
+        Geom g;
+        if ((st = check_geometry(sc.dims, sc.voxel_size, sc.origin, sc.det, sc.matrices, sc.n_views, &g))) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "scan %d: %s", s, g_err);
+            return fail(st, msg);
+        }
+        if (!sc.volume || (sc.n_views > 0 && !sc.projections)) return fail(FDK_ERR_INVALID_ARG, "scan has a null buffer");
+        if ((st = check_alignment(sc.volume, 4, "volume")) || (st = check_alignment(sc.projections, 4, "projections")))
+            return st;
+        if ((st = check_matrices(sc.matrices, sc.n_views, 0))) return st;
+        if ((st = check_device_ptr(sc.volume, "volume"))) return st;
+        if (sc.n_views > 0 && (st = check_device_ptr(sc.projections, "projections"))) return st;
+        if ((long long)g.W * (g.H + 1) >= (1LL << 23)) p->fidx = false;
+        total_views += (size_t)sc.n_views;
+    }
+    // one device buffer: descriptors | tile_start | counter | matrices | view indices
+    const size_t off_ts = sizeof(ScanDesc) * 2 * (size_t)n_scans;
+    const size_t off_ctr = off_ts + sizeof(int) * ((size_t)n_scans + 1);
+    const size_t off_mats = (off_ctr + sizeof(int) + 15) & ~(size_t)15;
+    const size_t off_vidx = off_mats + sizeof(float) * 12 * total_views;
+    const size_t bytes = off_vidx + sizeof(int) * total_views + 16;
+    if (cudaMalloc(&p->buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_OOM, "batch plan: device allocation failed");
+    }
+    char *base = static_cast<char *>(p->buf);
+    p->d_descs = reinterpret_cast<ScanDesc *>(base);
+    p->d_tile_start = reinterpret_cast<int *>(base + off_ts);
+    p->d_counter = reinterpret_cast<int *>(base + off_ctr);
+    std::vector<float> hm(12 * total_views);
+    std::vector<int> hv(total_views);
+    size_t at = 0;
+    for (int s = 0; s < n_scans; ++s) {
+        const fdk_scan &sc = scans[s];
+        for (int group = 0; group < 2; ++group) {
+            ScanDesc &d = p->h_descs[2 * s + group];
+            memset(&d, 0, sizeof d);
+            check_geometry(sc.dims, sc.voxel_size, sc.origin, sc.det, sc.matrices, sc.n_views, &d.g);
+            d.vol = sc.volume;
+            d.proj = sc.projections;
+            d.plane = (long long)sc.det[0] * sc.det[1];
+            d.mats_dev = reinterpret_cast<const float *>(base + off_mats) + 12 * at;
+            d.mats = nullptr;
+            d.vidx = reinterpret_cast<const int *>(base + off_vidx) + at;
+            int cnt = 0;
+            for (int k = 0; k < sc.n_views; ++k) {
+                const float *P = sc.matrices + 12 * (size_t)k;
+                const bool along_x = fabsf(P[8]) > fabsf(P[9]);
+                if (along_x != (group == 0)) continue;
+                memcpy(hm.data() + 12 * (at + cnt), P, sizeof(float) * 12);
+                hv[at + cnt] = k;
+                ++cnt;
+            }
+            d.n_views = cnt;
+            at += cnt;
+        }
+    }
+    cudaError_t e = cudaMemcpy(base + off_mats, hm.data(), sizeof(float) * hm.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_vidx, hv.data(), sizeof(int) * hv.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_descs, p->h_descs.data(), sizeof(ScanDesc) * p->h_descs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p->buf);
+        return fail(FDK_ERR_CUDA, "batch plan: upload failed");
+    }
+    st = autotune ? plan_autotune(p.get()) : plan_set_tile(p.get(), o.tile);
+    if (st) {
+        cudaFree(p->buf);
+        return st;
+    }
+    *plan = p.release();
+    return FDK_OK;
+}
+
+fdk_status fdk_batch_plan_execute(fdk_batch_plan plan, void *stream)
+{
+    g_err[0] = 0;
+    if (!plan) return fail(FDK_ERR_INVALID_ARG, "plan is null");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->dev) return fail(FDK_ERR_INVALID_ARG, "the plan's device is not current");
+    return plan_launch(plan, (cudaStream_t)stream);
+}
+
+fdk_status fdk_batch_plan_tile(fdk_batch_plan plan, int32_t *tile)
+{
+    g_err[0] = 0;
+    if (!plan || !tile) return fail(FDK_ERR_INVALID_ARG, "null argument");
+    *tile = plan->tile;
+    return FDK_OK;
+}
+
+void fdk_batch_plan_destroy(fdk_batch_plan plan)
+{
+    if (!plan) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->dev);
+    cudaFree(plan->buf);
+    cudaSetDevice(cur);
+    delete plan;
+}
+
+fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scans, const fdk_opts *opts)
+{
+    fdk_batch_plan plan = nullptr;
+    fdk_status st = fdk_batch_plan_create(&plan, scans, n_scans, opts);
+    if (st) return st;
+    cudaStream_t s = opts ? (cudaStream_t)opts->stream : nullptr;
+    st = fdk_batch_plan_execute(plan, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    fdk_batch_plan_destroy(plan);
+    if (st) return st;
+    if (e != cudaSuccess) {
+        set_error("batched back-projection: %s", cudaGetErrorString(e));
+        return FDK_ERR_CUDA;
+    }
+    return FDK_OK;
+}
+
+}  // extern "C"

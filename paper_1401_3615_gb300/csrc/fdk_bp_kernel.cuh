@@ -309,21 +309,19 @@ __device__ __forceinline__ void view_tex(float (&acc)[R], const ViewEntry &e, fl
     }
 }
 
-// CTA tile BX x BY x R; warps cover WX x (32/WX) voxel patches in (x, y).
-template <int BX, int BY, int WX, int R, int MINB, int KCHUNK, int FETCH, typename T, bool FIDX>
-__global__ void __launch_bounds__(BX * BY, MINB)
-fdk_bp_kernel(const __grid_constant__ BpArgs a)
+// Back-project every view of `a` into the BX x BY x R box at (x0, y0, z0):
+// per-thread register sums over all views, then one read-modify-write of the
+// box.  A is the launch's argument block (the kernel parameters of a plain
+// launch, or a scan descriptor of a batch); the shared tables are the
+// caller's.  Warps cover WX x (32/WX) voxel patches in (x, y).
+template <int BX, int BY, int WX, int R, int KCHUNK, int FETCH, typename T, bool FIDX, class A>
+__device__ __forceinline__ void bp_tile(const A &a, int x0, int y0, int z0, ViewEntry *tab,
+                                        unsigned char *cls, unsigned short *act, int *n_act_s)
 {
     static_assert(32 % WX == 0 && BX % WX == 0 && BY % (32 / WX) == 0, "warp tiling");
     static_assert(R % 2 == 0, "z-run must be even (voxel pairs)");
     constexpr int WY = 32 / WX;
     constexpr int WPX = BX / WX;
-    __shared__ ViewEntry tab[KCHUNK];
-    __shared__ unsigned char cls[KCHUNK];
-    __shared__ unsigned short act[KCHUNK];
-    __shared__ int n_act;
-
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = (warp % WPX) * WX + (lane % WX);
     const int ly = (warp / WPX) * WY + (lane / WX);
@@ -337,28 +335,32 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
 
     for (int v0 = 0; v0 < a.n_views; v0 += KCHUNK) {
         const int nv = min(KCHUNK, a.n_views - v0);
-        build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act);
-        const int n = n_act;
+        build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, n_act_s);
+        const int n = *n_act_s;
         for (int q = 0; q < n; ++q) {
             const int ev = act[q];
             const int lv = ev & 1023, c = ev >> 10;
             const int v = v0 + lv;
             const ViewEntry e = tab[lv];
-            if (FETCH == kTex) {
+            if constexpr (FETCH == kTex) {
                 const cudaTextureObject_t tex = (cudaTextureObject_t)a.tex[v];
                 if (c != kGeneral) view_tex<R, T, false>(acc, e, dxf, dyf, tex, W, H);
                 else view_tex<R, T, true>(acc, e, dxf, dyf, tex, W, H);
-            } else if (FETCH == kQuad && c != kGeneral) {
-                const void *qimg = static_cast<const char *>(a.quads) +
-                                   (long long)a.vidx[v] * a.qplane * (long long)sizeof(typename QuadType<T>::type);
-                if (c == kInterior) view_quad<R, T, false>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
-                else view_quad<R, T, true>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
-            } else {
-                const T *img = proj + (long long)a.vidx[v] * a.plane;
-                if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
-                else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
-                else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
+                continue;
             }
+            if constexpr (FETCH == kQuad) {
+                if (c != kGeneral) {
+                    const void *qimg = static_cast<const char *>(a.quads) +
+                                       (long long)a.vidx[v] * a.qplane * (long long)sizeof(typename QuadType<T>::type);
+                    if (c == kInterior) view_quad<R, T, false>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
+                    else view_quad<R, T, true>(acc, e, dxf, dyf, qimg, W, H, a.qpitch);
+                    continue;
+                }
+            }
+            const T *img = proj + (long long)a.vidx[v] * a.plane;
+            if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
+            else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
+            else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
         }
         __syncthreads();   // the next chunk overwrites the table
     }
@@ -375,11 +377,25 @@ fdk_bp_kernel(const __grid_constant__ BpArgs a)
     }
 }
 
+// One CTA per BX x BY x R tile of the volume (plain launch).
+template <int BX, int BY, int WX, int R, int MINB, int KCHUNK, int FETCH, typename T, bool FIDX>
+__global__ void __launch_bounds__(BX * BY, MINB)
+fdk_bp_kernel(const __grid_constant__ BpArgs a)
+{
+    __shared__ ViewEntry tab[KCHUNK];
+    __shared__ unsigned char cls[KCHUNK];
+    __shared__ unsigned short act[KCHUNK];
+    __shared__ int n_act;
+    bp_tile<BX, BY, WX, R, KCHUNK, FETCH, T, FIDX>(a, blockIdx.x * BX, blockIdx.y * BY, blockIdx.z * R,
+                                                    tab, cls, act, &n_act);
+}
+
 // CTA tile variants (BX x BY voxels in x, y; R voxels per thread along z;
 // minimum resident CTAs per SM for the register budget).  Warps cover 8 x 4
 // or 4 x 8 voxel patches (BpArgs::warp_x): views whose rays run mostly along
-// x project a 4 x 8 patch onto fewer L1 banks, views along y an 8 x 4 patch.  Index 0 is the default (the fastest at 512^3 x 496 views,
-// 1248 x 960) and shares its kernel with index 1.
+// x project a 4 x 8 patch onto fewer L1 banks, views along y an 8 x 4 patch.
+// Index 0 is the default (the fastest at 512^3 x 496 views, 1248 x 960) and
+// shares its kernel with index 1.
 struct TileCfg { int bx, by, r, minb; };
 constexpr int kNumTiles = 8;
 constexpr TileCfg kTiles[kNumTiles] = {

@@ -52,6 +52,29 @@ struct __align__(16) ViewEntry {
     float4 o;    // (U, V, V*W + U + 2^23, (V+2)*(W+3) + U + 2 + 2^23)
 };
 
+// One orientation group of one scan in a batch (device memory).  The field
+// names match BpArgs so the same tile code serves both.
+struct ScanDesc {
+    Geom g;
+    float *vol;
+    const void *proj;          // the scan's first image
+    long long plane;           // W*H
+    const float *mats_dev;     // this group's matrices, 12 per view
+    const float *mats;         // unused (always nullptr)
+    const int *vidx;           // image index of each view of the group
+    int n_views;               // views in this group
+    int pad;
+};
+
+// Arguments of one batched launch (device pointers).
+struct BatchLaunch {
+    const ScanDesc *descs;     // 2 per scan: views along x, views along y
+    const int *tile_start;     // n_scans + 1 prefix counts of (scan, tile) items
+    int *counter;              // work counter, zeroed before the launch
+    int n_scans;
+    int total;                 // work items
+};
+
 enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
 
 // Thread-local error message setter (fdk_api.cu).
@@ -60,6 +83,8 @@ void set_error(const char *fmt, ...);
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile,
                               cudaStream_t stream);
 void release_textures();
+fdk_status launch_batched(const BatchLaunch &b, int tile, bool fidx, cudaStream_t stream);
+void batched_tile_dims(int tile, int *bx, int *by, int *r);
 size_t quad_elem_size(int dtype);
 fdk_status launch_make_quads(const void *proj, void *quads, int n, int W, int H, int dtype,
                              cudaStream_t stream);

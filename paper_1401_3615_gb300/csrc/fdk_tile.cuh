@@ -50,8 +50,8 @@ constexpr unsigned kIndexBits = 0x4B000000u;
 // pixel against FP32 rounding and clipped to the image, and in wrange the
 // smallest and largest w of the tile's corners (of the whole tile, since w
 // is linear in the voxel position).
-template <int BX, int BY, int R>
-__device__ void build_view_table(const BpArgs &a, int v0, int nv, int x0, int y0, int z0,
+template <int BX, int BY, int R, class A>
+__device__ void build_view_table(const A &a, int v0, int nv, int x0, int y0, int z0,
                                  ViewEntry *tab, unsigned char *cls, unsigned short *act,
                                  int *n_act, int4 *bbox = nullptr, float2 *wrange = nullptr)
 {

@@ -33,7 +33,14 @@ class FdkError(RuntimeError):
 class fdk_opts(ctypes.Structure):
     _fields_ = [("proj_dtype", ctypes.c_int32), ("matrices_on_device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("fetch", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class fdk_scan(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_void_p), ("dims", ctypes.c_int32 * 3),
+                ("voxel_size", ctypes.c_float * 3), ("origin", ctypes.c_float * 3),
+                ("projections", ctypes.c_void_p), ("det", ctypes.c_int32 * 2),
+                ("matrices", ctypes.c_void_p), ("n_views", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -66,6 +73,18 @@ def _load():
                                               ctypes.c_int32, op]
             for fn in (lib.fdk_backproject, lib.fdk_forwardproject_adjoint, lib.fdk_count_updates):
                 fn.restype = ctypes.c_int
+            sp = ctypes.POINTER(fdk_scan)
+            pp = ctypes.POINTER(ctypes.c_void_p)
+            lib.fdk_batch_plan_create.argtypes = [pp, sp, ctypes.c_int32, op]
+            lib.fdk_batch_plan_create.restype = ctypes.c_int
+            lib.fdk_batch_plan_execute.argtypes = [vp, vp]
+            lib.fdk_batch_plan_execute.restype = ctypes.c_int
+            lib.fdk_batch_plan_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+            lib.fdk_batch_plan_tile.restype = ctypes.c_int
+            lib.fdk_batch_plan_destroy.argtypes = [vp]
+            lib.fdk_batch_plan_destroy.restype = None
+            lib.fdk_backproject_batched.argtypes = [sp, ctypes.c_int32, op]
+            lib.fdk_backproject_batched.restype = ctypes.c_int
             lib.fdk_last_error.restype = ctypes.c_char_p
             lib.fdk_last_error.argtypes = []
             lib.fdk_version.restype = ctypes.c_int32
@@ -210,3 +229,80 @@ def fdk_count_updates(dims, det, matrices, voxel_size, origin, *, stream=None) -
                                    _i32_2(int(det[0]), int(det[1])), mptr, n, ctypes.byref(o))
     _check(st)
     return int(out.value)
+
+
+def _scan_array(scans):
+    """scans: sequence of (volume, projections, matrices, voxel_size, origin)."""
+    arr = (fdk_scan * len(scans))()
+    keep = []
+    for s, (vol, proj, mats, vs, org) in zip(arr, scans):
+        if vol.dtype != torch.float32 or vol.dim() != 3 or not vol.is_contiguous():
+            raise ValueError("volume must be a contiguous float32 (nz, ny, nx) tensor")
+        if proj.dtype != torch.float32 or proj.dim() != 3 or not proj.is_contiguous():
+            raise ValueError("projections must be a contiguous float32 (n, H, W) tensor")
+        m = np.ascontiguousarray(np.asarray(mats.cpu() if isinstance(mats, torch.Tensor) else mats,
+                                            dtype=np.float32).reshape(-1, 12))
+        if m.shape[0] != proj.shape[0]:
+            raise ValueError("need one 3x4 matrix per view")
+        keep.append(m)
+        nz, ny, nx = vol.shape
+        s.volume = vol.data_ptr()
+        s.dims[:] = [nx, ny, nz]
+        s.voxel_size[:] = [float(x) for x in np.asarray(vs, dtype=np.float32).reshape(3)]
+        s.origin[:] = [float(x) for x in np.asarray(org, dtype=np.float32).reshape(3)]
+        s.projections = proj.data_ptr()
+        s.det[:] = [proj.shape[2], proj.shape[1]]
+        s.matrices = m.ctypes.data
+        s.n_views = proj.shape[0]
+    return arr, keep
+
+
+class BatchPlan:
+    """fdk_batch_plan_create / _execute / _tile / _destroy.  The tensors of
+    every scan must outlive the plan."""
+
+    def __init__(self, scans, *, tile: int = 0, autotune: bool = False):
+        arr, keep = _scan_array(scans)
+        o = fdk_opts()
+        o.tile = tile
+        o.autotune = 1 if autotune else 0
+        h = ctypes.c_void_p()
+        lib = _load()
+        _check(lib.fdk_batch_plan_create(ctypes.byref(h), arr, len(scans), ctypes.byref(o)))
+        self._h = h
+        self._lib = lib
+        self.scans = list(scans)
+
+    @property
+    def tile(self) -> int:
+        t = ctypes.c_int32(0)
+        _check(self._lib.fdk_batch_plan_tile(self._h, ctypes.byref(t)))
+        return int(t.value)
+
+    def execute(self, stream=None):
+        s = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
+        _check(self._lib.fdk_batch_plan_execute(self._h, ctypes.c_void_p(s)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fdk_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fdk_batch_plan_create(scans, *, tile: int = 0, autotune: bool = False) -> BatchPlan:
+    return BatchPlan(scans, tile=tile, autotune=autotune)
+
+
+def fdk_backproject_batched(scans, *, tile: int = 0, stream=None):
+    """One-shot batch: create a plan, execute it, synchronise, destroy."""
+    arr, keep = _scan_array(scans)
+    o = fdk_opts()
+    o.tile = tile
+    o.stream = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
+    _check(_load().fdk_backproject_batched(arr, len(scans), ctypes.byref(o)))
