@@ -183,6 +183,34 @@ FDK_API fdk_status fdk_backproject_static(float *volume, const int32_t dims[3],
                                           const float *matrices, int32_t n_views,
                                           const fdk_opts *opts);
 
+/*
+ * fdk_preweight_filter -- the FDK pre-processing that turns raw line
+ * integrals into the filtered projections fdk_backproject takes (the paper's
+ * data arrives in this form, Sec. IV):
+ *
+ *   out[k][n][m] = scale * sum_{m'} h(m - m') c_k(m', n) in[k][n][m']
+ *   h(0) = 1/4, h(d) = -1/(pi^2 d^2) for odd d, h(d) = 0 for even d != 0
+ *   c_k(m, n) = f / sqrt(f^2 + (m - u0)^2 + (n - v0)^2)
+ *
+ * a cosine pre-weight and a Ram-Lak (ramp) filter along every detector row,
+ * the kernel in pixel units: for the FDK weighting with w = depth/SID in the
+ * matrices, scale = d_beta / tau, the angular step over the detector pitch
+ * scaled to the isocentre (in the length unit of the line integrals).  (f, u0, v0) are
+ * read off each matrix through M M^T, assuming square pixels and no skew.
+ * The sum is a linear convolution over the row (zero outside it), computed
+ * by FFT on the device.
+ *
+ *  out, in      device, n_views*H*W FP32; out may equal in (in place).
+ *  det          host, {W, H}; W <= 4096.
+ *  matrices     n_views*12 FP32 row-major, host unless opts->matrices_on_device.
+ *  scale        finite.
+ * The first call for a row length on a device computes and caches the
+ * kernel's spectrum (a few KB; freed by fdk_release) and synchronises once.
+ */
+FDK_API fdk_status fdk_preweight_filter(float *out, const float *in, const int32_t det[2],
+                                        const float *matrices, int32_t n_views, float scale,
+                                        const fdk_opts *opts);
+
 /* One scan of a batch: the arguments of one fdk_backproject call (FP32
  * projections, host matrices). */
 typedef struct fdk_scan {

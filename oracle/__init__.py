@@ -58,8 +58,12 @@ def _load():
                                            ctypes.c_int64, _f32p, ctypes.c_int64, ctypes.c_int]
             lib.oracle_bruteforce.argtypes = [_f64p, _i64p, _f64p, _f64p, _f32p, ctypes.c_int64,
                                               ctypes.c_int64, _f32p, ctypes.c_int64]
+            lib.oracle_camera.argtypes = [_f32p, ctypes.c_int64, _f64p]
+            lib.oracle_preweight_filter.argtypes = [_f64p, _f32p, ctypes.c_int64, ctypes.c_int64,
+                                                    _f32p, ctypes.c_int64, ctypes.c_double]
             for fn in (lib.oracle_backproject, lib.oracle_backproject_voxels,
-                       lib.oracle_adjoint, lib.oracle_bruteforce):
+                       lib.oracle_adjoint, lib.oracle_bruteforce, lib.oracle_camera,
+                       lib.oracle_preweight_filter):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -158,3 +162,27 @@ def bruteforce(proj, mats, dims, voxel_size, origin) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_bruteforce failed ({rc})")
     return vol
+
+
+def camera(mats) -> np.ndarray:
+    """(n, 3) array of (f, u0, v0) per view, read off each matrix through
+    M M^T (square pixels, no skew)."""
+    m = np.ascontiguousarray(np.asarray(mats, dtype=np.float32).reshape(-1, 12))
+    out = np.zeros((m.shape[0], 3), dtype=np.float64)
+    if _load().oracle_camera(_p(m, _f32p), m.shape[0], _p(out, _f64p)) != 0:
+        raise ValueError("matrix is not a camera with square pixels")
+    return out
+
+
+def preweight_filter(proj, mats, scale: float = 1.0) -> np.ndarray:
+    """FP64 cosine pre-weighting and Ram-Lak row filtering of raw line
+    integrals (n, H, W) (direct linear convolution, small cases)."""
+    p = _proj(proj)
+    n, H, W = p.shape
+    m = _mats(mats, n)
+    out = np.zeros((n, H, W), dtype=np.float64)
+    rc = _load().oracle_preweight_filter(_p(out, _f64p), _p(p, _f32p), W, H, _p(m, _f32p), n,
+                                         float(scale))
+    if rc != 0:
+        raise RuntimeError(f"oracle_preweight_filter failed ({rc})")
+    return out

@@ -312,3 +312,78 @@ int oracle_bruteforce(double *vol, const int64_t dims[3], const double voxel_siz
             }
     return 0;
 }
+
+/*
+ * FDK pre-processing (the step before the back-projection; the paper's data
+ * arrives pre-filtered, Sec. IV): cosine pre-weighting and Ram-Lak filtering
+ * of every detector row, in FP64.
+ *
+ * The camera of view k is read off its matrix P = s K [R | t] with
+ * K = [[f, 0, u0], [0, f, v0], [0, 0, 1]] (square pixels, no skew): with
+ * M = P[:, 0:3], M M^T = s^2 K K^T, so s^2 = (M M^T)[2][2],
+ * u0 = (M M^T)[0][2] / s^2, v0 = (M M^T)[1][2] / s^2 and
+ * f^2 = (M M^T)[0][0] / s^2 - u0^2.  The cosine of the angle between the ray
+ * through pixel (m, n) and the principal axis is f / sqrt(f^2 + (m-u0)^2 +
+ * (n-v0)^2).  The row filter is the discrete Ram-Lak kernel in pixel units,
+ * h(0) = 1/4, h(d) = -1 / (pi^2 d^2) for odd d, 0 for even d != 0, applied
+ * as a linear convolution over the row (zero outside it):
+ *   out[k][n][m] = scale * sum_{m'} h(m - m') cos_k(m', n) in[k][n][m'].
+ */
+int oracle_camera(const float *mats, int64_t n_views, double *f_u0_v0)
+{
+    for (int64_t k = 0; k < n_views; ++k) {
+        const float *P = mats + 12 * k;
+        double G[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                G[a][b] = 0.0;
+                for (int c = 0; c < 3; ++c) G[a][b] += (double)P[4 * a + c] * (double)P[4 * b + c];
+            }
+        const double s2 = G[2][2];
+        if (!(s2 > 0.0)) return -1;
+        const double u0 = G[0][2] / s2, v0 = G[1][2] / s2;
+        const double f2 = G[0][0] / s2 - u0 * u0;
+        if (!(f2 > 0.0)) return -1;
+        f_u0_v0[3 * k + 0] = sqrt(f2);
+        f_u0_v0[3 * k + 1] = u0;
+        f_u0_v0[3 * k + 2] = v0;
+    }
+    return 0;
+}
+
+int oracle_preweight_filter(double *out, const float *proj, int64_t W, int64_t H,
+                            const float *mats, int64_t n_views, double scale)
+{
+    if (W <= 0 || H <= 0 || n_views < 0) return -1;
+    double *cam = (double *)malloc(sizeof(double) * 3 * (size_t)(n_views > 0 ? n_views : 1));
+    double *h = (double *)malloc(sizeof(double) * (size_t)W);
+    double *g = (double *)malloc(sizeof(double) * (size_t)W);
+    if (!cam || !h || !g) { free(cam); free(h); free(g); return -2; }
+    if (oracle_camera(mats, n_views, cam)) { free(cam); free(h); free(g); return -1; }
+    const double pi = 3.14159265358979323846;
+    for (int64_t d = 0; d < W; ++d)
+        h[d] = (d == 0) ? 0.25 : ((d % 2) ? -1.0 / (pi * pi * (double)d * (double)d) : 0.0);
+    for (int64_t k = 0; k < n_views; ++k) {
+        const double f = cam[3 * k], u0 = cam[3 * k + 1], v0 = cam[3 * k + 2];
+        for (int64_t n = 0; n < H; ++n) {
+            const float *row = proj + (k * H + n) * W;
+            for (int64_t m = 0; m < W; ++m) {
+                const double du = (double)m - u0, dv = (double)n - v0;
+                g[m] = (double)row[m] * f / sqrt(f * f + du * du + dv * dv);
+            }
+            double *o = out + (k * H + n) * W;
+            for (int64_t m = 0; m < W; ++m) {
+                double acc = 0.0;
+                for (int64_t mp = 0; mp < W; ++mp) {
+                    const int64_t d = m > mp ? m - mp : mp - m;
+                    acc += h[d] * g[mp];
+                }
+                o[m] = scale * acc;
+            }
+        }
+    }
+    free(cam);
+    free(h);
+    free(g);
+    return 0;
+}

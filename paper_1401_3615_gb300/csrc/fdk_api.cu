@@ -286,6 +286,52 @@ static void release_quads()
     cudaGetLastError();
 }
 
+// Ram-Lak spectra per (device, N), computed once and cached.
+struct Spectrum {
+    int dev, N;
+    float *spec;
+};
+static std::mutex g_spec_mu;
+static std::vector<Spectrum> g_spec;
+
+static fdk_status spectrum_get(int dev, int N, const float **out)
+{
+    std::lock_guard<std::mutex> lk(g_spec_mu);
+    for (auto &s : g_spec)
+        if (s.dev == dev && s.N == N) { *out = s.spec; return FDK_OK; }
+    float *p = nullptr;
+    if (cudaMalloc(&p, sizeof(float) * N) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_OOM, "filter spectrum allocation failed");
+    }
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    fdk_status st = launch_ramlak_spectrum(p, N, s);
+    if (st == FDK_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        st = fail(FDK_ERR_CUDA, "filter spectrum failed");
+    }
+    cudaStreamDestroy(s);
+    if (st) { cudaFree(p); return st; }
+    g_spec.push_back({dev, N, p});
+    *out = p;
+    return FDK_OK;
+}
+
+static void release_spectra()
+{
+    std::lock_guard<std::mutex> lk(g_spec_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &s : g_spec) {
+        cudaSetDevice(s.dev);
+        cudaFree(s.spec);
+    }
+    g_spec.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
 void release_textures()
 {
     std::lock_guard<std::mutex> lk(g_tex_mu);
@@ -315,6 +361,7 @@ void fdk_release(void)
 {
     release_textures();
     release_quads();
+    release_spectra();
 }
 
 fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float voxel_size[3],
@@ -897,3 +944,53 @@ fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scans, const
 }
 
 }  // extern "C"
+
+extern "C" fdk_status fdk_preweight_filter(float *out, const float *in, const int32_t det[2],
+                                           const float *matrices, int32_t n_views, float scale,
+                                           const fdk_opts *opts)
+{
+    g_err[0] = 0;
+    const fdk_opts *o = opts ? opts : &kDefaultOpts;
+    fdk_status st = check_opts(o);
+    if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
+    if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_INVALID_ARG, "the filter reads and writes FP32");
+    if (!det) return fail(FDK_ERR_INVALID_ARG, "det is null");
+    if (det[0] < 1 || det[1] < 1) return fail(FDK_ERR_INVALID_ARG, "det must be >= 1");
+    if (det[0] > 4096) return fail(FDK_ERR_INVALID_ARG, "the filter takes rows of at most 4096 pixels");
+    if (n_views < 0) return fail(FDK_ERR_INVALID_ARG, "n_views < 0");
+    if (!(scale > -3.0e38f && scale < 3.0e38f)) return fail(FDK_ERR_INVALID_ARG, "scale must be finite");
+    if (n_views == 0) return FDK_OK;
+    if (!out || !in || !matrices) return fail(FDK_ERR_INVALID_ARG, "null pointer");
+    if ((long long)det[0] * det[1] > ((long long)1 << 40) / n_views)
+        return fail(FDK_ERR_INVALID_ARG, "projection stack too large");
+    if ((st = check_alignment(out, 4, "out")) || (st = check_alignment(in, 4, "in"))) return st;
+    if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
+    if (!o->matrices_on_device) {
+        for (int k = 0; k < n_views; ++k) {
+            const float *P = matrices + 12 * (size_t)k;
+            if (!(P[8] * P[8] + P[9] * P[9] + P[10] * P[10] > 0.0f))
+                return fail(FDK_ERR_INVALID_ARG, "matrix row 3 is zero: not a camera");
+        }
+    }
+    if ((st = check_device_ptr(out, "out")) || (st = check_device_ptr(in, "in"))) return st;
+    if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
+    int N = 1;
+    while (N < 2 * det[0]) N <<= 1;
+    if (N < 4) N = 4;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const float *spec = nullptr;
+    if ((st = spectrum_get(dev, N, &spec))) return st;
+    cudaStream_t s = (cudaStream_t)o->stream;
+    const size_t plane = (size_t)det[0] * det[1];
+    for (int v0 = 0; v0 < n_views; v0 += KMAX) {
+        const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
+        if ((st = launch_filter(out + (size_t)v0 * plane, in + (size_t)v0 * plane, spec, scale,
+                                o->matrices_on_device ? nullptr : matrices + (size_t)v0 * 12,
+                                o->matrices_on_device ? matrices + (size_t)v0 * 12 : nullptr,
+                                det[0], det[1], nv, N, s)))
+            return st;
+    }
+    return FDK_OK;
+}

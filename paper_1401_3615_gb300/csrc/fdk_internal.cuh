@@ -83,6 +83,10 @@ void set_error(const char *fmt, ...);
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile,
                               cudaStream_t stream);
 void release_textures();
+fdk_status launch_ramlak_spectrum(float *spec, int N, cudaStream_t stream);
+fdk_status launch_filter(float *out, const float *in, const float *spec, float scale,
+                         const float *mats_host, const float *mats_dev, int W, int H, int n_views,
+                         int N, cudaStream_t stream);
 fdk_status launch_batched(const BatchLaunch &b, int tile, bool fidx, cudaStream_t stream);
 void batched_tile_dims(int tile, int *bx, int *by, int *r);
 size_t quad_elem_size(int dtype);

@@ -85,6 +85,8 @@ def _load():
             lib.fdk_batch_plan_destroy.restype = None
             lib.fdk_backproject_batched.argtypes = [sp, ctypes.c_int32, op]
             lib.fdk_backproject_batched.restype = ctypes.c_int
+            lib.fdk_preweight_filter.argtypes = [vp, vp, i3, vp, ctypes.c_int32, ctypes.c_float, op]
+            lib.fdk_preweight_filter.restype = ctypes.c_int
             lib.fdk_last_error.restype = ctypes.c_char_p
             lib.fdk_last_error.argtypes = []
             lib.fdk_version.restype = ctypes.c_int32
@@ -306,3 +308,21 @@ def fdk_backproject_batched(scans, *, tile: int = 0, stream=None):
     o.tile = tile
     o.stream = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
     _check(_load().fdk_backproject_batched(arr, len(scans), ctypes.byref(o)))
+
+
+def fdk_preweight_filter(out: torch.Tensor, raw: torch.Tensor, matrices, scale: float = 1.0,
+                         *, stream=None) -> torch.Tensor:
+    """out[n, H, W] = cosine pre-weighted, Ram-Lak row-filtered raw[n, H, W]
+    (CUDA FP32; out may be raw).  Returns ``out``."""
+    for t, name in ((out, "out"), (raw, "raw")):
+        if t.dtype != torch.float32 or t.dim() != 3 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 (n_views, H, W) tensor")
+    if out.shape != raw.shape:
+        raise ValueError("out and raw must have the same shape")
+    n = raw.shape[0]
+    m, mptr, mdev = _mats(matrices, n)
+    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+    st = _load().fdk_preweight_filter(_ptr(out), _ptr(raw), _i32_2(raw.shape[2], raw.shape[1]), mptr, n,
+                                      float(scale), ctypes.byref(o))
+    _check(st)
+    return out
