@@ -360,7 +360,7 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    # per-launch durations (one launch per 512 views), CUDA events on the launching stream
+    # per-launch durations (a step's launches run back to back), CUDA events on the launching stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
@@ -419,7 +419,7 @@ def run_ours(args):
                                    f"/ {ISSUE_SLOTS_PER_UPDATE} issue slots per update"),
                     "achieved_basis": (f"clipped updates {upd_clip:.4e} per step / step time "
                                        f"({passes} launches of the same kernel per step)"),
-                    "achieved_full_count": upd_full / (mean_launch * 1e-3) / 1e9}
+                    "achieved_full_count": upd_full / passes / (mean_launch * 1e-3) / 1e9}
         if clk.get("sm_mhz"):
             roofline["peak_at_measured_clock"] = peak_gups * clk["sm_mhz"] / sm_max
         cpu = None

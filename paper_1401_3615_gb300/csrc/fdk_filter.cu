@@ -9,7 +9,7 @@
 // skew).  The linear convolution along a row is evaluated as a circular one
 // of length N = 2^ceil(log2(2W)) >= 2W (so every lag |m - m'| < W is within
 // N/2 and nothing wraps): two rows are packed as the real and imaginary
-// parts of one complex signal, transformed by a radix-2 Stockham FFT in
+// parts of one complex signal, transformed by a radix-4 Stockham FFT in
 // shared memory, multiplied by the kernel's spectrum (real, since h is
 // even) and transformed back.
 #include <math.h>
@@ -53,22 +53,50 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// One N-point transform, src -> (ping-pong) -> result pointer returned.
-// Forward uses tw[t] = exp(-2 pi i t / N); inverse its conjugate.
+// One N-point transform (radix-4 Stockham passes, one radix-2 pass first
+// when log2 N is odd), src -> (ping-pong) -> result pointer returned.
+// Forward uses tw[t] = exp(-2 pi i t / N), t < 3N/4; inverse its conjugate.
 template <int NT>
 __device__ float2 *stockham(float2 *src, float2 *dst, const float2 *tw, int N, bool inverse)
 {
-    for (int Ns = 1; Ns < N; Ns <<= 1) {
-        const int tstep = N / (2 * Ns);
+    int Ns = 1;
+    if (!(__ffs(N) & 1)) {   // log2 N = ffs - 1 odd: one radix-2 pass, no twiddles
         for (int j = threadIdx.x; j < N / 2; j += NT) {
+            const float2 u = src[j], v = src[j + N / 2];
+            dst[2 * j] = make_float2(u.x + v.x, u.y + v.y);
+            dst[2 * j + 1] = make_float2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+        float2 *t = src;
+        src = dst;
+        dst = t;
+        Ns = 2;
+    }
+    const float sg = inverse ? -1.0f : 1.0f;
+    for (; Ns < N; Ns <<= 2) {
+        const int tstep = N / (4 * Ns);
+        for (int j = threadIdx.x; j < N / 4; j += NT) {
             const int k = j & (Ns - 1);
-            float2 w = tw[k * tstep];
-            if (inverse) w.y = -w.y;
-            const float2 u = src[j];
-            const float2 v = cmul(src[j + N / 2], w);
-            const int base = ((j - k) << 1) + k;
-            dst[base] = make_float2(u.x + v.x, u.y + v.y);
-            dst[base + Ns] = make_float2(u.x - v.x, u.y - v.y);
+            float2 w1 = tw[k * tstep], w2 = tw[2 * k * tstep], w3 = tw[3 * k * tstep];
+            w1.y *= sg;
+            w2.y *= sg;
+            w3.y *= sg;
+            const float2 a0 = src[j];
+            const float2 a1 = cmul(src[j + N / 4], w1);
+            const float2 a2 = cmul(src[j + N / 2], w2);
+            const float2 a3 = cmul(src[j + 3 * N / 4], w3);
+            // 4-point DFT: y_q = sum_m a_m (-i sg)^(m q)
+            const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
+            const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+            const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
+            const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+            // -i sg * d13 = (sg * d13.y, -sg * d13.x)
+            const float2 r = make_float2(sg * d13.y, -sg * d13.x);
+            const int base = ((j - k) << 2) + k;
+            dst[base] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            dst[base + Ns] = make_float2(d02.x + r.x, d02.y + r.y);
+            dst[base + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            dst[base + 3 * Ns] = make_float2(d02.x - r.x, d02.y - r.y);
         }
         __syncthreads();
         float2 *t = src;
@@ -85,7 +113,7 @@ fdk_filter_kernel(const __grid_constant__ FilterArgs a)
     extern __shared__ float2 sm[];
     const int N = a.N;
     float2 *b0 = sm, *b1 = sm + N, *tw = sm + 2 * N;
-    for (int t = threadIdx.x; t < N / 2; t += NT) {
+    for (int t = threadIdx.x; t < 3 * N / 4; t += NT) {
         float s, c;
         sincospif(-2.0f * (float)t / (float)N, &s, &c);
         tw[t] = make_float2(c, s);
@@ -167,7 +195,7 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, float s
     a.N = N;
     if (!mats_dev) memcpy(a.mats, mats_host, sizeof(float) * 12 * n_views);
     constexpr int NT = 256;
-    const size_t smem = sizeof(float2) * (size_t)(2 * N + N / 2);
+    const size_t smem = sizeof(float2) * (size_t)(2 * N + 3 * N / 4);
     cudaError_t err = cudaFuncSetAttribute(fdk_filter_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) {
         cudaGetLastError();
