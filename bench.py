@@ -125,6 +125,23 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(x: float, world: int, dev) -> float:
+    """The largest x over all ranks: a replicated job takes as long as its
+    slowest replica.  Needs an initialised process group when world > 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(world: int, updates_per_replica: float, seconds: float) -> float:
+    """Whole-job GUp/s: the updates of every replica over the slowest one's time."""
+    return world * updates_per_replica / seconds / 1e9
+
+
 def _cpu_sample(cfg, scan_proj, mats, dims, vs, org, target_s: float, threads: int):
     """Time the oracle on a central z-slab of the workload sized to about
     target_s seconds; returns (updates/s, description)."""
@@ -265,13 +282,9 @@ def _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, fwd_ms
         fdk.fdk_forwardproject_adjoint(out, vol, mats, vs, org)
     t1.record(stream)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = _max_over_ranks(t0.elapsed_time(t1) / steps, world, dev)
     del out
-    return {"value": world * upd_full / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+    return {"value": _job_rate(world, upd_full, ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "steps": steps, "ratio_to_forward": ms / fwd_ms,
             "what": "fdk_forwardproject_adjoint (transpose splat) on the same workload"}
 
@@ -303,12 +316,8 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - w0) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    return {"value": world * upd_full / e2e_s / 1e9, "unit": UNIT,
+    e2e_s = _max_over_ranks((time.perf_counter() - w0) / e2e_steps, world, dev)
+    return {"value": _job_rate(world, upd_full, e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
             "d2h_bytes_per_step": int(vol.numel() * vol.element_size())}
 
@@ -382,14 +391,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
+    total_ms = _max_over_ranks(t0.elapsed_time(t1), world, dev)
     launch_ms = [a.elapsed_time(b) / passes for a, b in ev]
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     ms_step = total_ms / args.steps
-    value = world * upd_full / (ms_step * 1e-3) / 1e9
+    value = _job_rate(world, upd_full, ms_step * 1e-3)
 
     precision = None
     if proj32 is not None:
@@ -450,7 +455,7 @@ def run_ours(args):
             "precision": precision,
             "gpu_launches": args.steps * passes,
             "clocks": clk,
-            "clipped_gups": world * upd_clip / (ms_step * 1e-3) / 1e9,
+            "clipped_gups": _job_rate(world, upd_clip, ms_step * 1e-3),
             "paper_context": {"xeon_phi_5110p_asm_512": PAPER_PHI_GUPS},
         }
         print(json.dumps(out), flush=True)
