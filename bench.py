@@ -35,12 +35,13 @@ FP32_LANES_PER_SM = 128
 ISSUE_SLOTS_PER_UPDATE = 27      # FP32 issue slots per update: 15 FP32 ops, 1 reciprocal, 2 floor, 2 int
                                  # conversions, 1 address, 2 bounds tests, 4 loads
 PAPER_PHI_GUPS = {"clipped": 8.5, "full": 12.9}   # Xeon Phi 5110P, assembly, 512^3
-# DRAM bytes (read + write) of one full-size back-projection launch from an
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only while
-# the kernel sources hash to the value they were taken with.
+# DRAM bytes (read + write) per back-projection launch, the mean of a step's
+# launches, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# valid only while the kernel sources hash to the value they were taken with.
 KERNEL_SOURCES = ["paper_1401_3615_gb300/csrc/fdk_bp_kernel.cuh", "paper_1401_3615_gb300/csrc/fdk_tile.cuh",
-                  "paper_1401_3615_gb300/csrc/fdk_internal.cuh", "paper_1401_3615_gb300/csrc/fdk_bp_ldg32.cu"]
-MEASURED_TRAFFIC = {("fdk512", 496, 0, 0): {"bytes": 19.28e9 + 0.558e9, "sources": "16788905c3c96344"}}
+                  "paper_1401_3615_gb300/csrc/fdk_internal.cuh", "paper_1401_3615_gb300/csrc/fdk_bp_ldg32.cu",
+                  "paper_1401_3615_gb300/csrc/fdk_bp_stage.cu"]
+MEASURED_TRAFFIC = {("fdk512", 496, 0, 0): {"bytes": 16788105728 / 2, "sources": "e840f83f541ee39c"}}
 
 
 def _sources_sha() -> str:

@@ -68,15 +68,26 @@ typedef enum fdk_dtype {
 } fdk_dtype;
 
 /* How the four taps are fetched.  AUTO picks the fastest path measured on
- * GB300, currently LDG. */
+ * GB300: STAGE where it applies (FP32 projections, W a multiple of 4, a
+ * 16-byte aligned base, tile 0, host matrices) and where the footprints of
+ * 16 x 16 x 8 voxel tiles fit its shared-memory stages (judged on the tile
+ * at the volume centre for up to 32 views; e.g. 0.5 mm voxels on 0.308 mm
+ * pixels at magnification 2), LDG otherwise.  STAGE and LDG give
+ * bitwise-equal results. */
 typedef enum fdk_fetch {
     FDK_FETCH_AUTO = 0,
     FDK_FETCH_LDG = 1,         /* read-only global loads, bounds checked per tile class */
     FDK_FETCH_TEX = 2,         /* 2x2 texture gather with zero border (taps in FP32); the
                                   images are first copied into cached CUDA arrays */
-    FDK_FETCH_QUAD = 3         /* one load per voxel from a zero-bordered "quad image" (each
+    FDK_FETCH_QUAD = 3,        /* one load per voxel from a zero-bordered "quad image" (each
                                   cell holds its 2x2 taps) built on the device per call in a
                                   cached staging buffer: 16 B per pixel (FP32), 8 B (FP16/BF16) */
+    FDK_FETCH_STAGE = 4        /* per (tile, view) the footprint is copied into shared memory
+                                  by the tensor-memory accelerator (zeros outside the image)
+                                  and the taps read from there; FP32 projections with W a
+                                  multiple of 4 and a 16-byte aligned base, tile 0 only, host
+                                  or device matrices; no staging memory.  A bounded wait that
+                                  gives up is reported by fdk_device_status() */
 } fdk_fetch;
 
 /* Optional knobs; pass NULL for defaults.  Zero in any field means default. */
@@ -264,6 +275,13 @@ FDK_API void fdk_batch_plan_destroy(fdk_batch_plan plan);
 /* Create, execute on opts->stream, synchronise that stream, destroy. */
 FDK_API fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scans,
                                            const fdk_opts *opts);
+
+/* Synchronise the current device, then report whether a bounded device-side
+ * wait of an earlier call on it gave up (FDK_ERR_TIMEOUT; the tiles whose
+ * wait gave up were left unwritten) or the device reported an error
+ * (FDK_ERR_CUDA).  Clears the timeout record.  Only the FDK_FETCH_STAGE path
+ * has such waits. */
+FDK_API fdk_status fdk_device_status(void);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 FDK_API const char *fdk_last_error(void);

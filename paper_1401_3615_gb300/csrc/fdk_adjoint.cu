@@ -110,9 +110,16 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     if (!(ftile > 0.0f)) return;   // uniform: an all-zero tile adds nothing
     ftile *= 1.0009765625f;         // headroom for the FP32 rounding of the sum
 
+    // The footprint buffer is used as two halves while boxes fit one: view q
+    // accumulates in the half that view q-1 is not being flushed from, so
+    // the flush of q-1 needs no barrier before the splat of q.  A box larger
+    // than a half takes the whole buffer after a barrier.  [prev_lo, prev_hi)
+    // is the cell range whose flush may still be in progress (uniform).
+    int prev_lo = 0, prev_hi = 0;
     for (int v0 = 0; v0 < a.n_views; v0 += kAdjChunk) {
         const int nv = min(kAdjChunk, a.n_views - v0);
         build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act, bbox, wrange);
+        prev_lo = prev_hi = 0;     // the table build ends with a barrier
         const int n = n_act;
         for (int q = 0; q < n; ++q) {
             const int ev = act[q];
@@ -131,6 +138,14 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
             const bool fixed = fits && wr.x > 0.0f && wr.y <= 1.5f * wr.x;
             const float scale = fixed ? 2147475456.0f * (wr.x * wr.x) / ftile : 0.0f;
             const float inv_scale = fixed ? ftile / (2147475456.0f * (wr.x * wr.x)) : 0.0f;
+            int *acc_v = acc_s;
+            if (fits) {
+                const int lo = (npx <= kAdjCap / 2 && prev_lo == 0 && prev_hi > 0) ? kAdjCap / 2 : 0;
+                if (lo < prev_hi && prev_lo < lo + npx) __syncthreads();   // that flush must be done
+                acc_v = acc_s + lo;
+                prev_lo = lo;
+                prev_hi = lo + npx;
+            }
             float *proj = proj_out + (long long)(v0 + lv) * a.plane;
             const float2 buv = __ffma2_rn(f2(dyf), f2(e.b.x, e.b.y), __ffma2_rn(f2(dxf), f2(e.a.z, e.a.w), f2(e.a.x, e.a.y)));
             const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
@@ -161,14 +176,14 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                     int i1 = (int)(__float_as_uint(t1.y) * bz + __float_as_uint(t1.x) + base);
                     i0 = min(max(i0, 0), hi_idx);
                     i1 = min(max(i1, 0), hi_idx);
-                    atomicAdd(acc_s + i0, __float2int_rn(k0.w00 * scale));
-                    atomicAdd(acc_s + i0 + 1, __float2int_rn(k0.w10 * scale));
-                    atomicAdd(acc_s + i0 + bb.z, __float2int_rn(k0.w01 * scale));
-                    atomicAdd(acc_s + i0 + bb.z + 1, __float2int_rn(k0.w11 * scale));
-                    atomicAdd(acc_s + i1, __float2int_rn(k1.w00 * scale));
-                    atomicAdd(acc_s + i1 + 1, __float2int_rn(k1.w10 * scale));
-                    atomicAdd(acc_s + i1 + bb.z, __float2int_rn(k1.w01 * scale));
-                    atomicAdd(acc_s + i1 + bb.z + 1, __float2int_rn(k1.w11 * scale));
+                    atomicAdd(acc_v + i0, __float2int_rn(k0.w00 * scale));
+                    atomicAdd(acc_v + i0 + 1, __float2int_rn(k0.w10 * scale));
+                    atomicAdd(acc_v + i0 + bb.z, __float2int_rn(k0.w01 * scale));
+                    atomicAdd(acc_v + i0 + bb.z + 1, __float2int_rn(k0.w11 * scale));
+                    atomicAdd(acc_v + i1, __float2int_rn(k1.w00 * scale));
+                    atomicAdd(acc_v + i1 + 1, __float2int_rn(k1.w10 * scale));
+                    atomicAdd(acc_v + i1 + bb.z, __float2int_rn(k1.w01 * scale));
+                    atomicAdd(acc_v + i1 + bb.z + 1, __float2int_rn(k1.w11 * scale));
                 }
             } else {
                 const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
@@ -188,10 +203,10 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                     if (c == kGeneral && !(wl > 0.0f)) g = 0.0f;
                     if (g == 0.0f) continue;
                     const Taps k = tap_weights(g, au, bv);
-                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i, j, k.w00);
-                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i + 1, j, k.w10);
-                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i, j + 1, k.w01);
-                    adj_tap_checked(acc_s, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i, j, k.w00);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j, k.w10);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i, j + 1, k.w01);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
                 }
             }
             if (fits) {
@@ -200,7 +215,7 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                 // zero when untouched and are reset to zero after the flush
                 if (VEC4) {
                     const int gw = bb.z >> 2;
-                    int4 *acc4 = reinterpret_cast<int4 *>(acc_s);
+                    int4 *acc4 = reinterpret_cast<int4 *>(acc_v);
                     for (int p = tid; p < (npx >> 2); p += NT) {
                         const int4 s4 = acc4[p];
                         if ((s4.x | s4.y | s4.z | s4.w) != 0) {
@@ -216,15 +231,14 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                     }
                 } else {
                     for (int p = tid; p < npx; p += NT) {
-                        const int s1 = acc_s[p];
+                        const int s1 = acc_v[p];
                         if (s1 != 0) {
                             const float v = fixed ? (float)s1 * inv_scale : __int_as_float(s1);
                             atomicAdd(proj + (long long)(bb.y + p / bb.z) * W + bb.x + p % bb.z, v);
-                            acc_s[p] = 0;
+                            acc_v[p] = 0;
                         }
                     }
                 }
-                __syncthreads();
             }
         }
         __syncthreads();   // the next chunk overwrites the table

@@ -68,7 +68,7 @@ static fdk_status check_opts(const fdk_opts *o)
         return fail(FDK_ERR_INVALID_ARG, "unknown proj_dtype");
     if (o->matrices_on_device != 0 && o->matrices_on_device != 1)
         return fail(FDK_ERR_INVALID_ARG, "matrices_on_device must be 0 or 1");
-    if (o->fetch < FDK_FETCH_AUTO || o->fetch > FDK_FETCH_QUAD)
+    if (o->fetch < FDK_FETCH_AUTO || o->fetch > FDK_FETCH_STAGE)
         return fail(FDK_ERR_INVALID_ARG, "unknown fetch path");
     if (o->tile < 0 || o->tile > 7) return fail(FDK_ERR_INVALID_ARG, "tile must be 0..7");
     if (o->autotune != 0 && o->autotune != 1) return fail(FDK_ERR_INVALID_ARG, "autotune must be 0 or 1");
@@ -286,6 +286,123 @@ static void release_quads()
     cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Staged path: tensor maps are encoded on the host per pass into the kernel
+// parameter block (no device memory).  The encoder is a driver entry point.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tmap_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// One map per box width over the pass's nv FP32 images (W x H x nv; the
+// row and image strides are multiples of 16 bytes because W % 4 == 0).
+static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
+{
+    EncodeTiledFn enc = tmap_encoder();
+    const cuuint64_t gdim[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nv};
+    const cuuint64_t gstride[2] = {(cuuint64_t)W * 4u, (cuuint64_t)W * (cuuint64_t)H * 4u};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    for (int m = 0; m < kNumBoxW; ++m) {
+        const cuuint32_t box[3] = {(cuuint32_t)box_width(m), (cuuint32_t)kBoxRows, 1};
+        CUresult r = enc(&a.tmap[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.proj), gdim,
+                         gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+            return FDK_ERR_CUDA;
+        }
+    }
+    return FDK_OK;
+}
+
+// Whether the staged path pays for this geometry: the 16 x 16 x 8 tile at
+// the volume centre is projected, as the kernel's table builder does, for up
+// to 32 views spread over the scan, and the path is taken when at least 90%
+// of its pixel boxes fit a stage (coarse voxels on a fine detector give
+// boxes too large to stage, and those views would fall back to LDG).
+static bool stage_pays(const Geom &g, const float *mats, int n_views)
+{
+    const int BX = 16, BY = 16, R = 8;
+    const int tx = (g.nx / 2) / BX * BX, ty = (g.ny / 2) / BY * BY, tz = (g.nz / 2) / R * R;
+    const int step = n_views > 32 ? n_views / 32 : 1;
+    int tried = 0, fit = 0;
+    for (int k = 0; k < n_views; k += step) {
+        const float *P = mats + (size_t)k * 12;
+        double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+        bool front = true;
+        for (int c = 0; c < 8; ++c) {
+            const double X = (double)g.org[0] + (double)(tx + ((c & 1) ? BX - 1 : 0)) * g.vs[0];
+            const double Y = (double)g.org[1] + (double)(ty + ((c & 2) ? BY - 1 : 0)) * g.vs[1];
+            const double Z = (double)g.org[2] + (double)(tz + ((c & 4) ? R - 1 : 0)) * g.vs[2];
+            const double w = P[8] * X + P[9] * Y + P[10] * Z + P[11];
+            if (!(w > 0.0)) { front = false; break; }
+            const double u = (P[0] * X + P[1] * Y + P[2] * Z + P[3]) / w;
+            const double v = (P[4] * X + P[5] * Y + P[6] * Z + P[7]) / w;
+            umin = std::min(umin, u); umax = std::max(umax, u);
+            vmin = std::min(vmin, v); vmax = std::max(vmax, v);
+        }
+        ++tried;
+        if (!front || umax - umin > 4096.0 || vmax - vmin > 4096.0) continue;
+        const long long i0 = (long long)floor(umin) - 1, i1 = (long long)floor(umax) + 2;
+        const long long j0 = (long long)floor(vmin) - 1, j1 = (long long)floor(vmax) + 2;
+        const long long wpx = i1 - (i0 & ~3LL) + 1;
+        const long long m = wpx <= 32 ? 0 : (wpx - 32 + 15) / 16;
+        const long long rows8 = (j1 - j0 + kBoxRows) / kBoxRows;
+        if (m < kNumBoxW && rows8 * kBoxRows * box_width((int)m) <= kStageFloats) ++fit;
+    }
+    return tried > 0 && fit * 10 >= tried * 9;
+}
+
+// One device word per device, set by a bounded wait that gave up.
+static std::mutex g_errw_mu;
+static std::vector<std::pair<int, unsigned *>> g_errw;
+
+static fdk_status err_word(int dev, unsigned **out)
+{
+    std::lock_guard<std::mutex> lk(g_errw_mu);
+    for (auto &p : g_errw)
+        if (p.first == dev) { *out = p.second; return FDK_OK; }
+    unsigned *w = nullptr;
+    if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess || cudaMemset(w, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        if (w) cudaFree(w);
+        return fail(FDK_ERR_OOM, "error-word allocation failed");
+    }
+    g_errw.push_back({dev, w});
+    *out = w;
+    return FDK_OK;
+}
+
+static void release_err_words()
+{
+    std::lock_guard<std::mutex> lk(g_errw_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &p : g_errw) {
+        cudaSetDevice(p.first);
+        cudaFree(p.second);
+    }
+    g_errw.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
 // Ram-Lak spectra per (device, N), computed once and cached.
 struct Spectrum {
     int dev, N;
@@ -362,6 +479,37 @@ void fdk_release(void)
     release_textures();
     release_quads();
     release_spectra();
+    release_err_words();
+}
+
+fdk_status fdk_device_status(void)
+{
+    g_err[0] = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        set_error("device error: %s", cudaGetErrorString(e));
+        return FDK_ERR_CUDA;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned *w = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_errw_mu);
+        for (auto &p : g_errw)
+            if (p.first == dev) w = p.second;
+    }
+    if (!w) return FDK_OK;
+    unsigned h = 0;
+    if (cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "reading the device error word failed");
+    }
+    if (h) {
+        cudaMemset(w, 0, sizeof(unsigned));
+        return fail(FDK_ERR_TIMEOUT, "a bounded wait of the staged back-projection gave up; "
+                                     "the tiles concerned were not written");
+    }
+    return FDK_OK;
 }
 
 fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float voxel_size[3],
@@ -392,21 +540,39 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     int dev = 0;
     cudaGetDevice(&dev);
 
-    // texture and quad paths only on request: on GB300 both measure slower
-    // than the LDG path at the 512^3 x 496-view, 1248 x 960 workload
+    // AUTO takes the staged path where it applies (FP32, tile 0, rows of a
+    // multiple of 16 bytes, 16-byte aligned images, host matrices) and pays
+    // (the tiles' pixel boxes fit a stage); it is bitwise equal to LDG and
+    // measures faster on GB300 there.  LDG elsewhere.  The texture and
+    // quad paths only on request: both measure slower than LDG.
+    int want = o->fetch;
+    if (want == FDK_FETCH_AUTO && o->proj_dtype == FDK_F32 && o->tile == 0 && g.W % 4 == 0 &&
+        ((uintptr_t)projections) % 16 == 0 && !o->matrices_on_device && tmap_encoder() &&
+        stage_pays(g, matrices, n_views))
+        want = FDK_FETCH_STAGE;
     bool use_tex = false, use_quad = false;
     TexStage *stage = nullptr;
     QuadStage *qstage = nullptr;
     std::unique_lock<std::mutex> lk(g_tex_mu, std::defer_lock);
     std::unique_lock<std::mutex> qlk(g_quad_mu, std::defer_lock);
     const int n_pass = n_views < KMAX ? n_views : KMAX;
-    if (o->fetch == FDK_FETCH_TEX) {
+    bool use_stage = false;
+    a.err = nullptr;
+    if (want == FDK_FETCH_STAGE) {
+        if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_UNSUPPORTED, "the staged path takes FP32 projections");
+        if (o->tile != 0) return fail(FDK_ERR_INVALID_ARG, "the staged path uses tile 0");
+        if (g.W % 4 != 0 || ((uintptr_t)projections) % 16 != 0)
+            return fail(FDK_ERR_UNSUPPORTED, "the staged path needs W % 4 == 0 and 16-byte aligned projections");
+        if (!tmap_encoder()) return fail(FDK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+        if ((st = err_word(dev, &a.err))) return st;
+        use_stage = true;
+    } else if (want == FDK_FETCH_TEX) {
         if (!tex_supported(dev, g.W, g.H))
             return fail(FDK_ERR_UNSUPPORTED, "detector exceeds the device's texture-gather size");
         lk.lock();
         if ((st = tex_stage_get(dev, g.W, g.H, o->proj_dtype, n_pass, &stage))) return st;
         use_tex = true;
-    } else if (o->fetch == FDK_FETCH_QUAD) {
+    } else if (want == FDK_FETCH_QUAD) {
         if (!quad_supported(g.W, g.H))
             return fail(FDK_ERR_UNSUPPORTED, "detector too large for quad images (2^23 cells)");
         qlk.lock();
@@ -422,6 +588,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     int fetch = 1;
     if (use_tex) fetch = 2;
     if (use_quad) fetch = 3;
+    if (use_stage) fetch = 4;
     for (int v0 = 0; v0 < n_views; v0 += KMAX) {
         const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
         a.g = g;
@@ -431,6 +598,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         a.quads = nullptr;
         a.qpitch = g.W + 3;
         a.qplane = (long long)(g.W + 3) * (g.H + 3);
+        if (use_stage && (st = encode_stage_maps(a, g.W, g.H, nv))) return st;
         if (use_tex) {
             for (int k = 0; k < nv; ++k) {
                 const char *src = static_cast<const char *>(a.proj) + (size_t)k * plane * esz;

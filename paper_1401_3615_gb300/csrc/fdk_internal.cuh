@@ -1,6 +1,7 @@
 // Internal declarations shared by the libfdk translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -15,6 +16,15 @@ namespace fdk {
 // them and concurrent calls on different streams cannot race.
 constexpr int KMAX = 512;
 
+// Staged fetch path: per (tile, view), the pixel box holding every tap of
+// the tile is copied into shared memory by TMA as a stack of 8-row boxes of
+// one of kNumBoxW widths (32, 48, ..., 128 pixels), at most kStageFloats
+// pixels; views whose box is larger keep the global-load path.
+constexpr int kNumBoxW = 7;
+constexpr int kBoxRows = 8;
+constexpr int kStageFloats = 3840;
+__host__ __device__ constexpr int box_width(int m) { return 32 + 16 * m; }
+
 struct Geom {
     int nx, ny, nz;
     int W, H;
@@ -22,7 +32,7 @@ struct Geom {
     float org[3];
 };
 
-// Everything one back-projection pass needs.  ~29 KB, under the 32 KB
+// Everything one back-projection pass needs.  ~31 KB, under the 32 KB
 // kernel-parameter limit.
 struct BpArgs {
     Geom g;
@@ -35,10 +45,16 @@ struct BpArgs {
     long long plane;           // W*H elements per image
     int n_views;               // views in this launch (<= KMAX)
     int warp_x;                // voxels along x per warp patch: 8 (8x4) or 4 (4x8)
+    unsigned *err;             // device word set when a bounded wait gives up (staged path)
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
-    unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
+    union {
+        unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
+        CUtensorMap tmap[kNumBoxW];    // staged path: the pass's images as a W x H x n
+                                       // tensor, one map per box width, 8-row boxes
+    };
     int vidx[KMAX];            // image index (within the pass's images) of each view
 };
+static_assert(sizeof(BpArgs) <= 32764, "kernel parameter block limit");
 
 // Per (tile, view) entry computed in each CTA's prologue (shared memory).
 // Detector coordinates are kept relative to an integer cell (U, V) near the
@@ -49,7 +65,8 @@ struct __align__(16) ViewEntry {
     float4 a;    // (c_u, c_v, gx_u, gx_v): value at the tile centre, step in x
     float4 b;    // (gy_u, gy_v, gz_u, gz_v): steps in y and z
     float4 w;    // (c_w, gx_w, gy_w, gz_w)
-    float4 o;    // (U, V, V*W + U + 2^23, (V+2)*(W+3) + U + 2 + 2^23)
+    float4 o;    // (U, V, V*W + U + 2^23, (V+2)*(W+3) + U + 2 + 2^23); staged views:
+                 // (U, V, (V-j0)*BW + U-x0 + 2^23, BW) for the box at (x0, j0), BW wide
 };
 
 // One orientation group of one scan in a batch (device memory).  The field
@@ -75,7 +92,7 @@ struct BatchLaunch {
     int total;                 // work items
 };
 
-enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3 };
+enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3, kStaged = 4 };
 
 // Thread-local error message setter (fdk_api.cu).
 void set_error(const char *fmt, ...);

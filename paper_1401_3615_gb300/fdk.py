@@ -18,7 +18,7 @@ from . import build as _build
 
 FDK_OK, FDK_ERR_INVALID_ARG, FDK_ERR_UNSUPPORTED, FDK_ERR_OOM, FDK_ERR_CUDA, FDK_ERR_TIMEOUT = range(6)
 FDK_F32, FDK_BF16, FDK_F16 = 0, 1, 2
-FETCH_AUTO, FETCH_LDG, FETCH_TEX, FETCH_QUAD = 0, 1, 2, 3
+FETCH_AUTO, FETCH_LDG, FETCH_TEX, FETCH_QUAD, FETCH_STAGE = 0, 1, 2, 3, 4
 _STATUS = {0: "FDK_OK", 1: "FDK_ERR_INVALID_ARG", 2: "FDK_ERR_UNSUPPORTED", 3: "FDK_ERR_OOM",
            4: "FDK_ERR_CUDA", 5: "FDK_ERR_TIMEOUT"}
 _DTYPES = {torch.float32: FDK_F32, torch.bfloat16: FDK_BF16, torch.float16: FDK_F16}
@@ -91,6 +91,8 @@ def _load():
             lib.fdk_last_error.argtypes = []
             lib.fdk_version.restype = ctypes.c_int32
             lib.fdk_release.restype = None
+            lib.fdk_device_status.argtypes = []
+            lib.fdk_device_status.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -105,6 +107,13 @@ def fdk_version() -> int:
 
 def fdk_release() -> None:
     _load().fdk_release()
+
+
+def fdk_device_status() -> None:
+    """Synchronise the current device; raise FdkError if a bounded
+    device-side wait of an earlier call gave up (FDK_ERR_TIMEOUT) or the
+    device reported an error."""
+    _check(_load().fdk_device_status())
 
 
 def _check(st: int):
