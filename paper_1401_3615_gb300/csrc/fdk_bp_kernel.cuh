@@ -128,14 +128,18 @@ __device__ __forceinline__ ViewBase view_base(const ViewEntry &e, float dxf, flo
 // Interior tiles: all four taps of every voxel lie inside the image.
 // FIDX: the flat tap index is formed in FP32 (exact while W*H < 2^23) and its
 // bit pattern used as the address offset; otherwise integer arithmetic.
+// Each f32x2 pair holds one quantity for two z neighbours, so every packed
+// operation finds its operands in place.
 template <int R, typename T, bool FIDX>
 __device__ __forceinline__ void view_interior_ldg(float (&acc)[R], const ViewEntry &e, float dxf,
                                                   float dyf, const T *img, int W)
 {
-    const ViewBase vb = view_base(e, dxf, dyf);
-    const float2 gz = f2(e.b.z, e.b.w);
-    const float2 M = f2(kFloorMagic);
-    const float Wf = (float)W;
+    const float2 BU = f2(fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x)));
+    const float2 BV = f2(fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y)));
+    const float2 BW = f2(fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x)));
+    const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
+    const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
+    const float2 PITCH = f2((float)W), OZ = f2(e.o.z);
     const int U = (int)e.o.x, V = (int)e.o.y;
     // row pointers biased so the index bits address the tap directly
     const unsigned long long row0 =
@@ -144,23 +148,22 @@ __device__ __forceinline__ void view_interior_ldg(float (&acc)[R], const ViewEnt
     const unsigned long long row1 = row0 + (unsigned long long)W * sizeof(T);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-        const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
-        const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(vb.w));
-        const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
-        const float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, vb.uv), f2(iw0));
-        const float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, vb.uv), f2(iw1));
-        const float2 t0 = __fadd2_rd(uv0, M), t1 = __fadd2_rd(uv1, M);
-        const float2 fl0 = __fadd2_rn(t0, f2(-kFloorMagic)), fl1 = __fadd2_rn(t1, f2(-kFloorMagic));
-        const float2 ab0 = __ffma2_rn(fl0, f2(-1.0f), uv0), ab1 = __ffma2_rn(fl1, f2(-1.0f), uv1);
+        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
+        const float2 wl = __ffma2_rn(RF, GW, BW);
+        const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
+        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
+        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 tu = __fadd2_rd(u, M), tv = __fadd2_rd(v, M);
+        const float2 flu = __fadd2_rn(tu, NM), flv = __fadd2_rn(tv, NM);
+        const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
         unsigned long long o0, o1;
         if (FIDX) {
-            const float2 s = __ffma2_rn(f2(fl0.y, fl1.y), f2(Wf), f2(fl0.x, fl1.x));
-            const float2 k = __fadd2_rn(s, f2(e.o.z));
+            const float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OZ);
             o0 = (unsigned long long)__float_as_uint(k.x) * sizeof(T);
             o1 = (unsigned long long)__float_as_uint(k.y) * sizeof(T);
         } else {
-            const int i0 = __float_as_int(t0.x) - kFloorBits + U, j0 = __float_as_int(t0.y) - kFloorBits + V;
-            const int i1 = __float_as_int(t1.x) - kFloorBits + U, j1 = __float_as_int(t1.y) - kFloorBits + V;
+            const int i0 = __float_as_int(tu.x) - kFloorBits + U, j0 = __float_as_int(tv.x) - kFloorBits + V;
+            const int i1 = __float_as_int(tu.y) - kFloorBits + U, j1 = __float_as_int(tv.y) - kFloorBits + V;
             o0 = (unsigned long long)(j0 * W + i0) * sizeof(T);
             o1 = (unsigned long long)(j1 * W + i1) * sizeof(T);
         }
@@ -168,12 +171,14 @@ __device__ __forceinline__ void view_interior_ldg(float (&acc)[R], const ViewEnt
         const T *q01 = reinterpret_cast<const T *>(row1 + o0);
         const T *q10 = reinterpret_cast<const T *>(row0 + o1);
         const T *q11 = reinterpret_cast<const T *>(row1 + o1);
-        const float v0 = bilerp(Elem<T>::load(q00), Elem<T>::load(q00 + 1), Elem<T>::load(q01),
-                                Elem<T>::load(q01 + 1), ab0);
-        const float v1 = bilerp(Elem<T>::load(q10), Elem<T>::load(q10 + 1), Elem<T>::load(q11),
-                                Elem<T>::load(q11 + 1), ab1);
-        const float2 w2 = __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1));
-        const float2 s2 = __ffma2_rn(f2(v0, v1), w2, f2(acc[r], acc[r + 1]));
+        const float2 p00 = f2(Elem<T>::load(q00), Elem<T>::load(q10));
+        const float2 p10 = f2(Elem<T>::load(q00 + 1), Elem<T>::load(q10 + 1));
+        const float2 p01 = f2(Elem<T>::load(q01), Elem<T>::load(q11));
+        const float2 p11 = f2(Elem<T>::load(q01 + 1), Elem<T>::load(q11 + 1));
+        const float2 lo = __ffma2_rn(au, __ffma2_rn(p00, NEG, p10), p00);
+        const float2 hi = __ffma2_rn(au, __ffma2_rn(p01, NEG, p11), p01);
+        const float2 val = __ffma2_rn(bv, __ffma2_rn(lo, NEG, hi), lo);
+        const float2 s2 = __ffma2_rn(val, __fmul2_rn(iw, iw), f2(acc[r], acc[r + 1]));
         acc[r] = s2.x;
         acc[r + 1] = s2.y;
     }

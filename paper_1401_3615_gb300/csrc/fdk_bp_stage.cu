@@ -88,36 +88,41 @@ __device__ __forceinline__ float lds(uint32_t addr)
 // Staged view: the taps come from the stage's box, BW = e.o.w pixels wide,
 // whose cell (U, V) sits at index e.o.z - 2^23.  No bounds checks: the box
 // holds every tap of the tile, with zeros where it extends past the image.
+// Each f32x2 pair holds one quantity for two z neighbours, so every packed
+// operation finds its operands in place.
 template <int R>
 __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e, float dxf, float dyf,
                                             const float *stage)
 {
-    const ViewBase vb = view_base(e, dxf, dyf);
-    const float2 gz = f2(e.b.z, e.b.w);
-    const float2 M = f2(kFloorMagic);
-    const float BWf = e.o.w;
-    const int BW = (int)BWf;
+    const float2 BU = f2(fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x)));
+    const float2 BV = f2(fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y)));
+    const float2 BW = f2(fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x)));
+    const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
+    const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
+    const float2 PITCH = f2(e.o.w), OZ = f2(e.o.z);
     // 32-bit shared addresses with the index magic folded into the base
     const uint32_t sbase = smem_addr(stage) - (kIndexBits << 2);
-    const uint32_t bw4 = (uint32_t)BW << 2;
+    const uint32_t bw4 = (uint32_t)(int)e.o.w << 2;
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-        const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
-        const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(vb.w));
-        const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
-        const float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, vb.uv), f2(iw0));
-        const float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, vb.uv), f2(iw1));
-        const float2 fl0 = __fadd2_rn(__fadd2_rd(uv0, M), f2(-kFloorMagic));
-        const float2 fl1 = __fadd2_rn(__fadd2_rd(uv1, M), f2(-kFloorMagic));
-        const float2 ab0 = __ffma2_rn(fl0, f2(-1.0f), uv0), ab1 = __ffma2_rn(fl1, f2(-1.0f), uv1);
-        const float2 s = __ffma2_rn(f2(fl0.y, fl1.y), f2(BWf), f2(fl0.x, fl1.x));
-        const float2 k = __fadd2_rn(s, f2(e.o.z));
+        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
+        const float2 wl = __ffma2_rn(RF, GW, BW);
+        const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
+        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
+        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
+        const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
+        const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
+        const float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OZ);
         const uint32_t a0 = sbase + ((uint32_t)__float_as_int(k.x) << 2);
         const uint32_t a1 = sbase + ((uint32_t)__float_as_int(k.y) << 2);
-        const float v0 = bilerp(lds(a0), lds(a0 + 4u), lds(a0 + bw4), lds(a0 + bw4 + 4u), ab0);
-        const float v1 = bilerp(lds(a1), lds(a1 + 4u), lds(a1 + bw4), lds(a1 + bw4 + 4u), ab1);
-        const float2 w2 = __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1));
-        const float2 s2 = __ffma2_rn(f2(v0, v1), w2, f2(acc[r], acc[r + 1]));
+        const float2 p00 = f2(lds(a0), lds(a1)), p10 = f2(lds(a0 + 4u), lds(a1 + 4u));
+        const float2 p01 = f2(lds(a0 + bw4), lds(a1 + bw4));
+        const float2 p11 = f2(lds(a0 + bw4 + 4u), lds(a1 + bw4 + 4u));
+        const float2 lo = __ffma2_rn(au, __ffma2_rn(p00, NEG, p10), p00);
+        const float2 hi = __ffma2_rn(au, __ffma2_rn(p01, NEG, p11), p01);
+        const float2 val = __ffma2_rn(bv, __ffma2_rn(lo, NEG, hi), lo);
+        const float2 s2 = __ffma2_rn(val, __fmul2_rn(iw, iw), f2(acc[r], acc[r + 1]));
         acc[r] = s2.x;
         acc[r + 1] = s2.y;
     }
