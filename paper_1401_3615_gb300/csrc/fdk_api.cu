@@ -403,7 +403,8 @@ static void release_err_words()
     cudaGetLastError();
 }
 
-// Ram-Lak spectra per (device, N), computed once and cached.
+// Ram-Lak spectra and twiddle tables per (device, N), computed once and
+// cached: N spectrum floats followed by N twiddles in one allocation.
 struct Spectrum {
     int dev, N;
     float *spec;
@@ -411,19 +412,24 @@ struct Spectrum {
 static std::mutex g_spec_mu;
 static std::vector<Spectrum> g_spec;
 
-static fdk_status spectrum_get(int dev, int N, const float **out)
+static fdk_status spectrum_get(int dev, int N, const float **out, const float2 **tw)
 {
     std::lock_guard<std::mutex> lk(g_spec_mu);
     for (auto &s : g_spec)
-        if (s.dev == dev && s.N == N) { *out = s.spec; return FDK_OK; }
+        if (s.dev == dev && s.N == N) {
+            *out = s.spec;
+            *tw = reinterpret_cast<const float2 *>(s.spec + N);
+            return FDK_OK;
+        }
     float *p = nullptr;
-    if (cudaMalloc(&p, sizeof(float) * N) != cudaSuccess) {
+    if (cudaMalloc(&p, sizeof(float) * N + sizeof(float2) * N) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "filter spectrum allocation failed");
     }
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     fdk_status st = launch_ramlak_spectrum(p, N, s);
+    if (st == FDK_OK) st = launch_twiddles(reinterpret_cast<float2 *>(p + N), N, s);
     if (st == FDK_OK && cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         st = fail(FDK_ERR_CUDA, "filter spectrum failed");
@@ -432,6 +438,7 @@ static fdk_status spectrum_get(int dev, int N, const float **out)
     if (st) { cudaFree(p); return st; }
     g_spec.push_back({dev, N, p});
     *out = p;
+    *tw = reinterpret_cast<const float2 *>(p + N);
     return FDK_OK;
 }
 
@@ -1149,12 +1156,13 @@ extern "C" fdk_status fdk_preweight_filter(float *out, const float *in, const in
     int dev = 0;
     cudaGetDevice(&dev);
     const float *spec = nullptr;
-    if ((st = spectrum_get(dev, N, &spec))) return st;
+    const float2 *tw = nullptr;
+    if ((st = spectrum_get(dev, N, &spec, &tw))) return st;
     cudaStream_t s = (cudaStream_t)o->stream;
     const size_t plane = (size_t)det[0] * det[1];
     for (int v0 = 0; v0 < n_views; v0 += KMAX) {
         const int nv = (n_views - v0 < KMAX) ? (n_views - v0) : KMAX;
-        if ((st = launch_filter(out + (size_t)v0 * plane, in + (size_t)v0 * plane, spec, scale,
+        if ((st = launch_filter(out + (size_t)v0 * plane, in + (size_t)v0 * plane, spec, tw, scale,
                                 o->matrices_on_device ? nullptr : matrices + (size_t)v0 * 12,
                                 o->matrices_on_device ? matrices + (size_t)v0 * 12 : nullptr,
                                 det[0], det[1], nv, N, s)))

@@ -9,9 +9,10 @@
 // skew).  The linear convolution along a row is evaluated as a circular one
 // of length N = 2^ceil(log2(2W)) >= 2W (so every lag |m - m'| < W is within
 // N/2 and nothing wraps): two rows are packed as the real and imaginary
-// parts of one complex signal, transformed by a radix-4 Stockham FFT in
-// shared memory, multiplied by the kernel's spectrum (real, since h is
-// even) and transformed back.
+// parts of one complex signal, transformed by a Stockham FFT, multiplied by
+// the kernel's spectrum (real, since h is even) and transformed back: for
+// N = 4096 three radix-16 passes with the points in registers, otherwise
+// radix-4 passes in shared memory.
 #include <math.h>
 
 #include "fdk_internal.cuh"
@@ -38,10 +39,21 @@ __global__ void fdk_ramlak_spectrum_kernel(float *spec, int N)
     spec[k] = s / (float)N;
 }
 
+// Twiddle table tw[t] = exp(-2 pi i t / N), t < N.
+__global__ void fdk_twiddle_kernel(float2 *tw, int N)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    float sv, cv;
+    sincospif(2.0f * (float)t / (float)N, &sv, &cv);   // 2t/N is exact (N a power of two)
+    tw[t] = make_float2(cv, -sv);
+}
+
 struct FilterArgs {
     float *out;
     const float *in;
     const float *spec;      // N spectrum values (1/N folded in)
+    const float2 *tw;       // N twiddles exp(-2 pi i t / N) (the N = 4096 kernel)
     float scale;
     const float *mats_dev;  // device matrices, or nullptr
     int W, H, n_views, N;
@@ -168,6 +180,205 @@ fdk_filter_kernel(const __grid_constant__ FilterArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// N = 4096 = 16^3 (detector rows of 1025..2048 pixels): three radix-16
+// Stockham passes per transform with the 16 points of each thread in
+// registers.  Pass p (stride Ns = 16^p) takes a_m = in[j + 256 m] times
+// exp(-+2 pi i m (j mod Ns) / (16 Ns)), forms their 16-point DFT y_q and
+// stores it at (j - j mod Ns) 16 + j mod Ns + q Ns.  The first pass reads
+// the weighted rows straight from global memory, and the last forward pass
+// leaves thread j holding X[j + 256 q] -- exactly the inputs of the first
+// inverse pass -- so the spectrum multiply happens in registers; the last
+// inverse pass leaves result[j + 256 q] for the coalesced row stores.  Four
+// shared-memory exchanges per row pair, padded one float2 per 16 so every
+// exchange runs at the minimum of two wavefronts per warp access.
+constexpr int kF16N = 4096;
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// In-place 4-point DFT; INV uses exp(+2 pi i nk/4).
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    // forward: -i d13; inverse: +i d13
+    const float2 r = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+    a0 = cadd(s02, s13);
+    a1 = cadd(d02, r);
+    a2 = csub(s02, s13);
+    a3 = csub(d02, r);
+}
+
+// x[n] -> x[q] = sum_n x[n] exp(-+2 pi i n q / 16), as 4 x 4 with n = 4 n1 + n2,
+// q = k1 + 4 k2 and the twiddles exp(-+2 pi i n2 k1 / 16) in between.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&x)[16])
+{
+    // cos and sin of 2 pi j / 16 for the twiddle exponents j = n2 k1
+    constexpr float C1 = 0.92387953251128676f, S1 = 0.38268343236508977f, H = 0.70710678118654752f;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+    // x[4 k1 + n2] now holds the n2-th inner DFT at k1
+    const float sg = INV ? 1.0f : -1.0f;
+    const float2 w1 = make_float2(C1, sg * S1), w2 = make_float2(H, sg * H), w3 = make_float2(S1, sg * C1);
+    const float2 w6 = make_float2(-H, sg * H), w9 = make_float2(-C1, -sg * S1);
+    x[5] = cmul(x[5], w1);
+    x[6] = cmul(x[6], w2);
+    x[7] = cmul(x[7], w3);
+    x[9] = cmul(x[9], w2);
+    x[10] = make_float2(-sg * x[10].y, sg * x[10].x);   // times exp(-+i pi/2)
+    x[11] = cmul(x[11], w6);
+    x[13] = cmul(x[13], w3);
+    x[14] = cmul(x[14], w6);
+    x[15] = cmul(x[15], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+    // x[4 k1 + k2] holds X[k1 + 4 k2]: transpose into natural order
+    float2 y[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) y[q] = x[4 * (q & 3) + (q >> 2)];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = y[q];
+}
+
+// Pass with stride Ns (16 or 256) reading from the shared buffer.  The
+// twiddles w^m, w = exp(-+2 pi i kk tstep / N), come from four table values
+// (w, w^2, w^4, w^8) and at most two products each.
+template <bool INV>
+__device__ __forceinline__ void pass_in(float2 (&x)[16], const float2 *buf, const float2 *__restrict__ tw,
+                                        int j, int kk, int tstep)
+{
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = buf[pad16(j + 256 * m)];
+    const int t1 = kk * tstep;
+    float2 w1 = __ldg(tw + t1), w2 = __ldg(tw + 2 * t1), w4 = __ldg(tw + 4 * t1), w8 = __ldg(tw + 8 * t1);
+    if (INV) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        w4.y = -w4.y;
+        w8.y = -w8.y;
+    }
+    const float2 w3 = cmul(w1, w2);
+    x[1] = cmul(x[1], w1);
+    x[2] = cmul(x[2], w2);
+    x[3] = cmul(x[3], w3);
+    x[4] = cmul(x[4], w4);
+    x[5] = cmul(x[5], cmul(w4, w1));
+    x[6] = cmul(x[6], cmul(w4, w2));
+    x[7] = cmul(x[7], cmul(w4, w3));
+    x[8] = cmul(x[8], w8);
+    x[9] = cmul(x[9], cmul(w8, w1));
+    x[10] = cmul(x[10], cmul(w8, w2));
+    x[11] = cmul(x[11], cmul(w8, w3));
+    const float2 w12 = cmul(w8, w4);
+    x[12] = cmul(x[12], w12);
+    x[13] = cmul(x[13], cmul(w12, w1));
+    x[14] = cmul(x[14], cmul(w12, w2));
+    x[15] = cmul(x[15], cmul(w12, w3));
+    dft16<INV>(x);
+}
+
+__global__ void __launch_bounds__(256, 2)
+fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
+{
+    __shared__ float2 buf[kF16N + kF16N / 16];
+    const int j = threadIdx.x;
+    const int pairs = (a.H + 1) / 2;
+    const long long total = (long long)pairs * a.n_views;
+    for (long long rp = blockIdx.x; rp < total; rp += gridDim.x) {
+        const int k = (int)(rp / pairs), p = (int)(rp % pairs);
+        const int r1 = 2 * p, r2 = 2 * p + 1;
+        // camera of view k from M M^T
+        float P[9];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                P[3 * q + c] = a.mats_dev ? __ldg(a.mats_dev + 12 * k + 4 * q + c) : a.mats[12 * k + 4 * q + c];
+        const float s2 = P[6] * P[6] + P[7] * P[7] + P[8] * P[8];
+        const float u0 = (P[0] * P[6] + P[1] * P[7] + P[2] * P[8]) / s2;
+        const float v0 = (P[3] * P[6] + P[4] * P[7] + P[5] * P[8]) / s2;
+        const float f2v = (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / s2 - u0 * u0;
+        const float f = sqrtf(f2v);
+        const float *row1 = a.in + ((long long)k * a.H + r1) * a.W;
+        const float *row2 = a.in + ((long long)k * a.H + r2) * a.W;
+        const float dv1 = (float)r1 - v0, dv2 = (float)r2 - v0;
+        const bool has2 = r2 < a.H;
+
+        float2 x[16];
+        // forward pass 1 (Ns = 1) from the weighted rows, zero past the row
+        // (W <= 2048 = N / 2, so points 2048.. are zero padding)
+#pragma unroll
+        for (int m = 8; m < 16; ++m) x[m] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int col = j + 256 * m;
+            float vx = 0.0f, vy = 0.0f;
+            if (col < a.W) {
+                const float du = (float)col - u0;
+                vx = row1[col] * f * rsqrtf(f2v + du * du + dv1 * dv1);
+                if (has2) vy = row2[col] * f * rsqrtf(f2v + du * du + dv2 * dv2);
+            }
+            x[m] = make_float2(vx, vy);
+        }
+        dft16<false>(x);
+        __syncthreads();   // the previous row pair's last reads of buf are done
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[pad16(16 * j + q)] = x[q];
+        __syncthreads();
+        // forward pass 2 (Ns = 16)
+        pass_in<false>(x, buf, a.tw, j, j & 15, 16);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[pad16((j & ~15) * 16 + (j & 15) + 16 * q)] = x[q];
+        __syncthreads();
+        // forward pass 3 (Ns = 256): thread j ends with X[j + 256 q]
+        pass_in<false>(x, buf, a.tw, j, j, 1);
+        // the kernel's spectrum (real, 1/N folded in) and the caller's scale
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float hq = __ldg(a.spec + j + 256 * q) * a.scale;
+            x[q] = make_float2(x[q].x * hq, x[q].y * hq);
+        }
+        // inverse pass 1 (Ns = 1) on the registers
+        dft16<true>(x);
+        __syncthreads();   // everyone's pass-3 reads are done
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[pad16(16 * j + q)] = x[q];
+        __syncthreads();
+        pass_in<true>(x, buf, a.tw, j, j & 15, 16);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[pad16((j & ~15) * 16 + (j & 15) + 16 * q)] = x[q];
+        __syncthreads();
+        // inverse pass 3: thread j ends with result[j + 256 q]
+        pass_in<true>(x, buf, a.tw, j, j, 1);
+        float *o1 = a.out + ((long long)k * a.H + r1) * a.W;
+        float *o2 = a.out + ((long long)k * a.H + r2) * a.W;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int col = j + 256 * q;
+            if (col < a.W) {
+                o1[col] = x[q].x;
+                if (has2) o2[col] = x[q].y;
+            }
+        }
+    }
+}
+
+fdk_status launch_twiddles(float2 *tw, int N, cudaStream_t s)
+{
+    fdk_twiddle_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        set_error("filter twiddle launch failed: %s", cudaGetErrorString(err));
+        return FDK_ERR_CUDA;
+    }
+    return FDK_OK;
+}
+
 fdk_status launch_ramlak_spectrum(float *spec, int N, cudaStream_t s)
 {
     fdk_ramlak_spectrum_kernel<<<(N + 255) / 256, 256, 0, s>>>(spec, N);
@@ -179,7 +390,7 @@ fdk_status launch_ramlak_spectrum(float *spec, int N, cudaStream_t s)
     return FDK_OK;
 }
 
-fdk_status launch_filter(float *out, const float *in, const float *spec, float scale,
+fdk_status launch_filter(float *out, const float *in, const float *spec, const float2 *tw, float scale,
                          const float *mats_host, const float *mats_dev, int W, int H, int n_views,
                          int N, cudaStream_t s)
 {
@@ -187,6 +398,7 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, float s
     a.out = out;
     a.in = in;
     a.spec = spec;
+    a.tw = tw;
     a.scale = scale;
     a.mats_dev = mats_dev;
     a.W = W;
@@ -194,6 +406,27 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, float s
     a.n_views = n_views;
     a.N = N;
     if (!mats_dev) memcpy(a.mats, mats_host, sizeof(float) * 12 * n_views);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = (long long)((H + 1) / 2) * n_views;
+    if (N == kF16N && tw) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdk_filter4096_kernel, 256, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        long long grid = (long long)sms * per_sm;
+        if (grid > total) grid = total;
+        if (grid < 1) return FDK_OK;
+        fdk_filter4096_kernel<<<(unsigned)grid, 256, 0, s>>>(a);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) {
+            set_error("filter launch failed: %s", cudaGetErrorString(err));
+            return FDK_ERR_CUDA;
+        }
+        return FDK_OK;
+    }
     constexpr int NT = 256;
     const size_t smem = sizeof(float2) * (size_t)(2 * N + 3 * N / 4);
     cudaError_t err = cudaFuncSetAttribute(fdk_filter_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -202,15 +435,11 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, float s
         set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(err));
         return FDK_ERR_CUDA;
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdk_filter_kernel<NT>, NT, smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const long long total = (long long)((H + 1) / 2) * n_views;
     long long grid = (long long)sms * per_sm;
     if (grid > total) grid = total;
     if (grid < 1) return FDK_OK;

@@ -2,7 +2,11 @@
 filter, fdk_preweight_filter) against the FP64 oracle's direct convolution.
 
 The device computes the row convolution by FFT in FP32; the bar is
-max|diff| <= 1e-5 max|q| (FFT rounding grows like log2 N times FP32 eps).
+max|diff| <= 3e-5 max|q| with PSNR >= 100 dB.  An independent FP32 route --
+the same weights and zero-padded circular convolution through a
+single-precision (complex64) FFT library on the host -- measures 1.4e-5 of
+max|q| on the 2048 x 2 case below and 8e-6 on 1248 x 5, so the bar is about
+twice what FP32 FFT arithmetic itself reaches on full 2048-pixel rows.
 """
 import numpy as np
 import pytest
@@ -14,7 +18,7 @@ from _helpers import assert_parity
 from paper_1401_3615_gb300 import fdk
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-5
+TOL = 3e-5
 
 
 def _raw(cfg):
@@ -23,7 +27,8 @@ def _raw(cfg):
     return raw, geo["mats"]
 
 
-@pytest.mark.parametrize("W,H", [(64, 48), (1, 5), (33, 7), (128, 3), (1000, 4)])
+@pytest.mark.parametrize("W,H", [(64, 48), (1, 5), (33, 7), (128, 3), (1000, 4),
+                                 (1025, 3), (1248, 5), (2048, 2)])
 def test_filter_parity_shapes(W, H):
     cfg = synth.preset("small", n_views=3, det_w=W, det_h=H, pixel=0.308 * 1248.0 / W)
     raw, mats = _raw(cfg)
@@ -43,6 +48,21 @@ def test_filter_in_place_multi_pass_and_device_matrices():
     ref = oracle.preweight_filter(raw.cpu().numpy(), mats, scale=1.0)
     x = raw.clone()
     fdk.fdk_preweight_filter(x, x, mats)                     # in place, two passes of views
+    y = torch.empty_like(raw)
+    fdk.fdk_preweight_filter(y, raw, torch.from_numpy(mats).cuda())
+    torch.cuda.synchronize()
+    assert_parity(ref, x.cpu().numpy(), rel_tol=TOL, psnr_min=100)
+    assert torch.equal(x, y)
+
+
+def test_filter_4096_in_place_two_passes_device_matrices():
+    """Rows of 1028 pixels (the N = 4096 register-FFT kernel): 520 views in
+    two passes of views, in place, and with device matrices."""
+    cfg = synth.preset("small", n_views=520, det_w=1028, det_h=3, pixel=0.308 * 1248.0 / 1028)
+    raw, mats = _raw(cfg)
+    ref = oracle.preweight_filter(raw.cpu().numpy(), mats, scale=1.0)
+    x = raw.clone()
+    fdk.fdk_preweight_filter(x, x, mats)
     y = torch.empty_like(raw)
     fdk.fdk_preweight_filter(y, raw, torch.from_numpy(mats).cuda())
     torch.cuda.synchronize()
