@@ -41,7 +41,7 @@ PAPER_PHI_GUPS = {"clipped": 8.5, "full": 12.9}   # Xeon Phi 5110P, assembly, 51
 KERNEL_SOURCES = ["paper_1401_3615_gb300/csrc/fdk_bp_kernel.cuh", "paper_1401_3615_gb300/csrc/fdk_tile.cuh",
                   "paper_1401_3615_gb300/csrc/fdk_internal.cuh", "paper_1401_3615_gb300/csrc/fdk_bp_ldg32.cu",
                   "paper_1401_3615_gb300/csrc/fdk_bp_stage.cu"]
-MEASURED_TRAFFIC = {("fdk512", 496, 0, 0): {"bytes": 16788105728 / 2, "sources": "e840f83f541ee39c"}}
+MEASURED_TRAFFIC = {("fdk512", 496, 0, 0): {"bytes": 16220539520 / 2, "sources": "61340b0590301d09"}}
 
 
 def _sources_sha() -> str:
@@ -290,6 +290,45 @@ def _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, fwd_ms
             "what": "fdk_forwardproject_adjoint (transpose splat) on the same workload"}
 
 
+def _preprocess_timing(args, world, dev, proj, mats, cfg):
+    """Time the FDK pre-processing step on the workload's images: cosine
+    pre-weighting and Ram-Lak row filtering (fdk_preweight_filter) of n raw
+    line-integral images into filtered ones.  The step's projections serve
+    as the raw input (the values do not change the work)."""
+    import torch
+    from paper_1401_3615_gb300 import fdk
+    out = torch.empty_like(proj)
+    dbeta = np.deg2rad(cfg.arc_deg) / max(cfg.n_views - 1, 1)
+    scale = float(dbeta / (cfg.pixel * cfg.sid / cfg.sdd))
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        fdk.fdk_preweight_filter(out, proj, mats, scale)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fdk.fdk_preweight_filter(out, proj, mats, scale)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = _max_over_ranks(t0.elapsed_time(t1) / steps, world, dev)
+    del out
+    nbytes = 2 * proj.numel() * 4
+    hbm = float(_peaks().get("hbm_gbs", 6800.0))
+    return {"ms_per_step": ms, "steps": steps, "GB_per_s": nbytes / (ms * 1e-3) / 1e9,
+            "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "bytes": nbytes,
+            "what": (f"fdk_preweight_filter: cosine pre-weight + Ram-Lak row filter of {proj.shape[0]} images "
+                     f"of {proj.shape[2]}x{proj.shape[1]} (row FFT length {_fft_len(proj.shape[2])})")}
+
+
+def _fft_len(W: int) -> int:
+    n = 1
+    while n < 2 * W:
+        n <<= 1
+    return max(n, 4)
+
+
 def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     """End to end through the public API with host buffers: every step copies
     the projections from pinned host memory to the device, back-projects
@@ -405,6 +444,10 @@ def run_ours(args):
     if not args.no_adjoint and proj32 is None:
         adjoint = _adjoint_timing(args, world, dev, proj, vol, mats, vs, org, upd_full, ms_step)
 
+    preprocess = None
+    if not args.no_preprocess and proj32 is None:
+        preprocess = _preprocess_timing(args, world, dev, proj, mats, cfg)
+
     e2e = None
     if not args.no_e2e:
         e2e = _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full)
@@ -453,6 +496,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "adjoint": adjoint,
+            "preprocess": preprocess,
             "precision": precision,
             "gpu_launches": args.steps * passes,
             "clocks": clk,
@@ -543,6 +587,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-preprocess", action="store_true")
     ap.add_argument("--batched", action="store_true", help="time the batched form instead")
     ap.add_argument("--batch-scans", type=int, default=32)
     ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
