@@ -573,6 +573,34 @@ def run_batched(args):
     return 0
 
 
+def run_micro(args):
+    """Gather micro-benchmarks (the GB300 counterpart of the paper's gather
+    table, Sec. V): one JSON line."""
+    import torch
+    from paper_1401_3615_gb300 import fdk
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    res = {
+        "ldg_warp_loads_per_sm_cycle_by_lines": {str(d): fdk.fdk_microbench(fdk.MICRO_LDG, d)
+                                                 for d in (1, 2, 4, 8, 16, 32)},
+        "lds_warp_loads_per_sm_cycle_by_conflict": {str(c): fdk.fdk_microbench(fdk.MICRO_LDS, c)
+                                                    for c in (1, 2, 4, 8, 32)},
+        "tld4_warp_gathers_per_sm_cycle": {str(n): fdk.fdk_microbench(fdk.MICRO_TLD4, n) for n in (64, 1248)},
+        "rcp_warp_instr_per_sm_cycle": fdk.fdk_microbench(fdk.MICRO_RCP, 0),
+        "dependent_load_cycles_by_ring_kib": {str(k): fdk.fdk_microbench(fdk.MICRO_CHASE, k)
+                                              for k in (16, 32768, 1048576)},
+    }
+    line = {"metric": "gather micro-benchmarks", "impl": "ours", "n_gpus": 1, "data": "synthetic",
+            "results": res,
+            "notes": ("warp loads / SM / cycle for 4-byte loads whose 32 lanes touch 1..32 distinct 128-byte "
+                      "lines (L1-resident); shared loads at 1..32-way bank conflicts; 2x2 texture gathers; "
+                      "rcp.approx; one thread's dependent-load latency over 16 KiB (L1), 32 MiB (L2) and "
+                      "1 GiB (HBM) rings")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,6 +617,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-preprocess", action="store_true")
     ap.add_argument("--batched", action="store_true", help="time the batched form instead")
+    ap.add_argument("--micro", action="store_true", help="run the gather micro-benchmarks instead")
     ap.add_argument("--batch-scans", type=int, default=32)
     ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
     ap.add_argument("--proj-dtype", default="f32", choices=["f32", "bf16", "f16"],
@@ -598,6 +627,8 @@ def main():
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.micro:
+        return run_micro(args)
     return run_ours(args)
 
 

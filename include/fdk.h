@@ -283,6 +283,30 @@ FDK_API fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scan
  * has such waits. */
 FDK_API fdk_status fdk_device_status(void);
 
+/* Gather micro-benchmarks of the device (the GB300 counterpart of the
+ * paper's gather measurements, Sec. V, Table II).  Synchronous; allocates
+ * and frees its own scratch memory (up to param KiB for FDK_MICRO_CHASE).
+ *   FDK_MICRO_LDG    warp-wide 4-byte loads from L1-resident data whose 32
+ *                    lanes touch `param` distinct 128-byte lines (param
+ *                    divides 32) -> warp loads per SM per cycle
+ *   FDK_MICRO_LDS    shared-memory loads with a `param`-way bank conflict
+ *                    (param divides 32) -> warp loads per SM per cycle
+ *   FDK_MICRO_TLD4   2x2 texture gathers at random texels of a param x param
+ *                    FP32 texture (2..4096) -> warp gathers per SM per cycle
+ *   FDK_MICRO_RCP    rcp.approx -> warp instructions per SM per cycle
+ *   FDK_MICRO_CHASE  one thread's dependent loads over a param-KiB ring
+ *                    (1 KiB .. 4 GiB) -> cycles per load
+ * The SM clock is measured alongside.  INVALID_ARG for an unknown
+ * benchmark or parameter, OOM when scratch cannot be allocated. */
+typedef enum fdk_micro {
+    FDK_MICRO_LDG = 1,
+    FDK_MICRO_LDS = 2,
+    FDK_MICRO_TLD4 = 3,
+    FDK_MICRO_RCP = 4,
+    FDK_MICRO_CHASE = 5
+} fdk_micro;
+FDK_API fdk_status fdk_microbench(int32_t which, int32_t param, double *result);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 FDK_API const char *fdk_last_error(void);
 

@@ -93,6 +93,8 @@ def _load():
             lib.fdk_release.restype = None
             lib.fdk_device_status.argtypes = []
             lib.fdk_device_status.restype = ctypes.c_int
+            lib.fdk_microbench.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+            lib.fdk_microbench.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -114,6 +116,17 @@ def fdk_device_status() -> None:
     device-side wait of an earlier call gave up (FDK_ERR_TIMEOUT) or the
     device reported an error."""
     _check(_load().fdk_device_status())
+
+
+MICRO_LDG, MICRO_LDS, MICRO_TLD4, MICRO_RCP, MICRO_CHASE = 1, 2, 3, 4, 5
+
+
+def fdk_microbench(which: int, param: int = 0) -> float:
+    """One gather micro-benchmark of the current device (see include/fdk.h):
+    warp operations per SM per cycle, or cycles per load for MICRO_CHASE."""
+    out = ctypes.c_double(0.0)
+    _check(_load().fdk_microbench(int(which), int(param), ctypes.byref(out)))
+    return float(out.value)
 
 
 def _check(st: int):
