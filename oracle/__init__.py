@@ -47,7 +47,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # FDK_ORACLE_LIB names another build of fdk_oracle.c to load instead;
+            # the mutation tests use it to run the pins against planted mistakes
+            lib = ctypes.CDLL(os.environ.get("FDK_ORACLE_LIB") or build())
             lib.oracle_backproject.argtypes = [_f64p, _i64p, _f64p, _f64p, _f32p, ctypes.c_int64,
                                                ctypes.c_int64, _f32p, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_int]
