@@ -1158,6 +1158,8 @@ extern "C" fdk_status fdk_preweight_filter(float *out, const float *in, const in
     const float *spec = nullptr;
     const float2 *tw = nullptr;
     if ((st = spectrum_get(dev, N, &spec, &tw))) return st;
+    unsigned *errw = nullptr;
+    if ((st = err_word(dev, &errw))) return st;
     cudaStream_t s = (cudaStream_t)o->stream;
     const size_t plane = (size_t)det[0] * det[1];
     for (int v0 = 0; v0 < n_views; v0 += KMAX) {
@@ -1165,7 +1167,7 @@ extern "C" fdk_status fdk_preweight_filter(float *out, const float *in, const in
         if ((st = launch_filter(out + (size_t)v0 * plane, in + (size_t)v0 * plane, spec, tw, scale,
                                 o->matrices_on_device ? nullptr : matrices + (size_t)v0 * 12,
                                 o->matrices_on_device ? matrices + (size_t)v0 * 12 : nullptr,
-                                det[0], det[1], nv, N, s)))
+                                det[0], det[1], nv, N, errw, s)))
             return st;
     }
     return FDK_OK;

@@ -54,6 +54,7 @@ struct FilterArgs {
     const float *in;
     const float *spec;      // N spectrum values (1/N folded in)
     const float2 *tw;       // N twiddles exp(-2 pi i t / N) (the N = 4096 kernel)
+    unsigned *err;          // device word set when a bounded wait gives up (staged rows)
     float scale;
     const float *mats_dev;  // device matrices, or nullptr
     int W, H, n_views, N;
@@ -280,14 +281,83 @@ __device__ __forceinline__ void pass_in(float2 (&x)[16], const float2 *buf, cons
     dft16<INV>(x);
 }
 
+constexpr long long kFilterWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t fsmem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bounded wait for the phase with the given parity of the mbarrier at bar.
+__device__ __forceinline__ bool fmbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < kFilterWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Copy the rows of row pair rp into a stage (rows 2048 floats apart) with
+// bulk copies completing on the mbarrier at bar.  Called by one thread.
+__device__ __forceinline__ void filter_issue(const FilterArgs &a, long long rp, int pairs, float *stage,
+                                             uint32_t bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the stage's last reads
+    const int k = (int)(rp / pairs), p = (int)(rp % pairs);
+    const int r1 = 2 * p, r2 = 2 * p + 1;
+    const uint32_t rowbytes = (uint32_t)a.W * 4u;
+    const uint32_t bytes = r2 < a.H ? 2u * rowbytes : rowbytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    const float *row1 = a.in + ((long long)k * a.H + r1) * a.W;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(fsmem(stage)), "l"(row1), "r"(rowbytes), "r"(bar) : "memory");
+    if (r2 < a.H)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(fsmem(stage + kF16N / 2)), "l"(row1 + a.W), "r"(rowbytes), "r"(bar) : "memory");
+}
+
+// STAGED: the rows (W % 4 == 0, 16-byte aligned) of the row pair after next
+// are copied into one of two shared-memory stages while this one is
+// transformed, so the first pass reads its inputs from shared memory.
+template <bool STAGED>
 __global__ void __launch_bounds__(256, 2)
 fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
 {
-    __shared__ float2 buf[kF16N + kF16N / 16];
+    extern __shared__ __align__(128) float2 fsm[];
+    float2 *buf = fsm;                                               // padded transform buffer
+    float *stages = reinterpret_cast<float *>(fsm + kF16N + kF16N / 16);   // 2 x (2 rows of 2048)
+    __shared__ __align__(8) unsigned long long full[2];
     const int j = threadIdx.x;
     const int pairs = (a.H + 1) / 2;
     const long long total = (long long)pairs * a.n_views;
-    for (long long rp = blockIdx.x; rp < total; rp += gridDim.x) {
+    const long long stride = gridDim.x;
+    const uint32_t full0 = fsmem(full);
+    unsigned nis[2] = {0u, 0u};   // copies issued into each stage (thread 0)
+    if (STAGED) {
+        if (j == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full0) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full0 + 8u) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (j == 0) {
+            for (int q = 0; q < 2; ++q) {
+                const long long rq = blockIdx.x + q * stride;
+                if (rq < total) {
+                    filter_issue(a, rq, pairs, stages + q * kF16N, full0 + 8u * q);
+                    ++nis[q];
+                }
+            }
+        }
+    }
+    int it = 0;
+    for (long long rp = blockIdx.x; rp < total; rp += stride, ++it) {
         const int k = (int)(rp / pairs), p = (int)(rp % pairs);
         const int r1 = 2 * p, r2 = 2 * p + 1;
         // camera of view k from M M^T
@@ -302,8 +372,17 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
         const float v0 = (P[3] * P[6] + P[4] * P[7] + P[5] * P[8]) / s2;
         const float f2v = (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / s2 - u0 * u0;
         const float f = sqrtf(f2v);
-        const float *row1 = a.in + ((long long)k * a.H + r1) * a.W;
-        const float *row2 = a.in + ((long long)k * a.H + r2) * a.W;
+        const float *row1, *row2;
+        const int st = it & 1;
+        bool ok = true;
+        if (STAGED) {
+            row1 = stages + st * kF16N;
+            row2 = row1 + kF16N / 2;
+            ok = fmbar_wait(full0 + 8u * st, (unsigned)(it >> 1) & 1u);
+        } else {
+            row1 = a.in + ((long long)k * a.H + r1) * a.W;
+            row2 = a.in + ((long long)k * a.H + r2) * a.W;
+        }
         const float dv1 = (float)r1 - v0, dv2 = (float)r2 - v0;
         const bool has2 = r2 < a.H;
 
@@ -324,7 +403,24 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
             x[m] = make_float2(vx, vy);
         }
         dft16<false>(x);
-        __syncthreads();   // the previous row pair's last reads of buf are done
+        // the previous row pair's last reads of buf, and this one's reads of
+        // its stage, are done
+        if (STAGED) {
+            if (!__syncthreads_and(ok)) {
+                if (j == 0) {
+                    atomicOr(a.err, 1u);
+                    for (int q = 0; q < 2; ++q)
+                        if (nis[q] > 0) fmbar_wait(full0 + 8u * q, (nis[q] - 1) & 1u);
+                }
+                return;
+            }
+            if (j == 0 && rp + 2 * stride < total) {
+                filter_issue(a, rp + 2 * stride, pairs, stages + st * kF16N, full0 + 8u * st);
+                ++nis[st];
+            }
+        } else {
+            __syncthreads();
+        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) buf[pad16(16 * j + q)] = x[q];
         __syncthreads();
@@ -392,13 +488,14 @@ fdk_status launch_ramlak_spectrum(float *spec, int N, cudaStream_t s)
 
 fdk_status launch_filter(float *out, const float *in, const float *spec, const float2 *tw, float scale,
                          const float *mats_host, const float *mats_dev, int W, int H, int n_views,
-                         int N, cudaStream_t s)
+                         int N, unsigned *err, cudaStream_t s)
 {
     static thread_local FilterArgs a;
     a.out = out;
     a.in = in;
     a.spec = spec;
     a.tw = tw;
+    a.err = err;
     a.scale = scale;
     a.mats_dev = mats_dev;
     a.W = W;
@@ -411,28 +508,38 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long total = (long long)((H + 1) / 2) * n_views;
     if (N == kF16N && tw) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdk_filter4096_kernel, 256, 0) != cudaSuccess ||
-            per_sm < 1) {
+        // rows staged by bulk copies when each row is a whole number of
+        // 16-byte units starting on a 16-byte boundary
+        const bool staged = err && W % 4 == 0 && ((uintptr_t)in % 16) == 0;
+        auto k = staged ? fdk_filter4096_kernel<true> : fdk_filter4096_kernel<false>;
+        const int smem = (int)(sizeof(float2) * (kF16N + kF16N / 16) + (staged ? sizeof(float) * 2 * kF16N : 0));
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(e));
+            return FDK_ERR_CUDA;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
         long long grid = (long long)sms * per_sm;
         if (grid > total) grid = total;
         if (grid < 1) return FDK_OK;
-        fdk_filter4096_kernel<<<(unsigned)grid, 256, 0, s>>>(a);
-        cudaError_t err = cudaGetLastError();
-        if (err != cudaSuccess) {
-            set_error("filter launch failed: %s", cudaGetErrorString(err));
+        k<<<(unsigned)grid, 256, smem, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("filter launch failed: %s", cudaGetErrorString(e));
             return FDK_ERR_CUDA;
         }
         return FDK_OK;
     }
     constexpr int NT = 256;
     const size_t smem = sizeof(float2) * (size_t)(2 * N + 3 * N / 4);
-    cudaError_t err = cudaFuncSetAttribute(fdk_filter_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) {
+    cudaError_t e = cudaFuncSetAttribute(fdk_filter_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(err));
+        set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(e));
         return FDK_ERR_CUDA;
     }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdk_filter_kernel<NT>, NT, smem) != cudaSuccess ||
@@ -444,9 +551,9 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
     if (grid > total) grid = total;
     if (grid < 1) return FDK_OK;
     fdk_filter_kernel<NT><<<(unsigned)grid, NT, smem, s>>>(a);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) {
-        set_error("filter launch failed: %s", cudaGetErrorString(err));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("filter launch failed: %s", cudaGetErrorString(e));
         return FDK_ERR_CUDA;
     }
     return FDK_OK;

@@ -104,7 +104,7 @@ fdk_status launch_ramlak_spectrum(float *spec, int N, cudaStream_t stream);
 fdk_status launch_twiddles(float2 *tw, int N, cudaStream_t stream);
 fdk_status launch_filter(float *out, const float *in, const float *spec, const float2 *tw, float scale,
                          const float *mats_host, const float *mats_dev, int W, int H, int n_views,
-                         int N, cudaStream_t stream);
+                         int N, unsigned *err, cudaStream_t stream);
 fdk_status launch_batched(const BatchLaunch &b, int tile, bool fidx, cudaStream_t stream);
 void batched_tile_dims(int tile, int *bx, int *by, int *r);
 size_t quad_elem_size(int dtype);
