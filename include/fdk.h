@@ -70,10 +70,10 @@ typedef enum fdk_dtype {
 /* How the four taps are fetched.  AUTO picks the fastest path measured on
  * GB300: STAGE where it applies (FP32 projections, W a multiple of 4, a
  * 16-byte aligned base, tile 0, host matrices) and where the footprints of
- * 16 x 16 x 8 voxel tiles fit its shared-memory stages (judged on the tile
+ * its 16 x 16 x 16 voxel tiles fit its shared-memory stages (judged on the tile
  * at the volume centre for up to 32 views; e.g. 0.5 mm voxels on 0.308 mm
- * pixels at magnification 2), LDG otherwise.  STAGE and LDG give
- * bitwise-equal results. */
+ * pixels at magnification 2), LDG otherwise.  STAGE gives the same bits as
+ * LDG with the same tile (tile variant 7, 16 x 16 x 16). */
 typedef enum fdk_fetch {
     FDK_FETCH_AUTO = 0,
     FDK_FETCH_LDG = 1,         /* read-only global loads, bounds checked per tile class */
@@ -85,9 +85,10 @@ typedef enum fdk_fetch {
     FDK_FETCH_STAGE = 4        /* per (tile, view) the footprint is copied into shared memory
                                   by the tensor-memory accelerator (zeros outside the image)
                                   and the taps read from there; FP32 projections with W a
-                                  multiple of 4 and a 16-byte aligned base, tile 0 only, host
-                                  or device matrices; no staging memory.  A bounded wait that
-                                  gives up is reported by fdk_device_status() */
+                                  multiple of 4 and a 16-byte aligned base, opts->tile 0 (the
+                                  path's own 16 x 16 x 16 tiles), host or device matrices; no
+                                  staging memory.  A bounded wait that gives up is reported by
+                                  fdk_device_status() */
 } fdk_fetch;
 
 /* Optional knobs; pass NULL for defaults.  Zero in any field means default. */
@@ -259,8 +260,8 @@ FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *s
  * NULL = legacy default stream): a reset of the plan's work counter and one
  * persistent kernel in which CTAs take (scan, tile) items from that counter
  * until none are left.  Every volume is accumulated (+=) exactly as by
- * fdk_backproject with the plan's tile variant, bit for bit.  It allocates
- * nothing and does not synchronise.  Executions of one plan must not
+ * fdk_backproject with FDK_FETCH_LDG and the plan's tile variant, bit for
+ * bit.  It allocates nothing and does not synchronise.  Executions of one plan must not
  * overlap on the GPU (they share the counter); the plan's device must be
  * current.
  */

@@ -63,7 +63,7 @@ __device__ __forceinline__ Taps tap_weights(float g, float a, float b)
 // VEC4: rows of the projections are 16-byte aligned (W % 4 == 0 and an
 // aligned base), so footprint boxes are widened to 4-pixel groups and
 // flushed with one vector atomic per group.
-template <int BX, int BY, int R, bool VEC4>
+template <int BX, int BY, int R, int WX, bool VEC4>
 __global__ void __launch_bounds__(BX * BY, 3)
 fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
 {
@@ -82,7 +82,8 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
 
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * R;
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int WX = 8, WY = 4, WPX = BX / WX;
+    static_assert(32 % WX == 0 && BX % WX == 0 && BY % (32 / WX) == 0, "warp tiling");
+    constexpr int WY = 32 / WX, WPX = BX / WX;
     const int lx = (warp % WPX) * WX + (lane % WX);
     const int ly = (warp / WPX) * WY + (lane / WX);
     const float dxf = (float)(lx - BX / 2), dyf = (float)(ly - BY / 2);
@@ -146,7 +147,7 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                 prev_lo = lo;
                 prev_hi = lo + npx;
             }
-            float *proj = proj_out + (long long)(v0 + lv) * a.plane;
+            float *proj = proj_out + (long long)a.vidx[v0 + lv] * a.plane;
             const float2 buv = __ffma2_rn(f2(dyf), f2(e.b.x, e.b.y), __ffma2_rn(f2(dxf), f2(e.a.z, e.a.w), f2(e.a.x, e.a.y)));
             const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
             const float2 gz = f2(e.b.z, e.b.w);
@@ -245,12 +246,13 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     }
 }
 
-fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t s)
+template <int WX>
+static fdk_status launch_adjoint_wx(const BpArgs &a, float *proj_out, cudaStream_t s)
 {
     dim3 grid((a.g.nx + kAdjBX - 1) / kAdjBX, (a.g.ny + kAdjBY - 1) / kAdjBY, (a.g.nz + kAdjR - 1) / kAdjR);
     const bool vec4 = (a.g.W % 4) == 0 && ((uintptr_t)proj_out % 16) == 0;
     const size_t smem = (size_t)kAdjCap * sizeof(int);
-    auto k = vec4 ? fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, true> : fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, false>;
+    auto k = vec4 ? fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, WX, true> : fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, WX, false>;
     // opt in to more than 48 KB of dynamic shared memory (idempotent)
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) {
@@ -265,6 +267,17 @@ fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t s)
         return FDK_ERR_CUDA;
     }
     return FDK_OK;
+}
+
+// Warp patches of a.warp_x voxels along x by 32 / a.warp_x along y.
+fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t s)
+{
+    switch (a.warp_x) {
+    case 2: return launch_adjoint_wx<2>(a, proj_out, s);
+    case 4: return launch_adjoint_wx<4>(a, proj_out, s);
+    case 16: return launch_adjoint_wx<16>(a, proj_out, s);
+    default: return launch_adjoint_wx<8>(a, proj_out, s);
+    }
 }
 
 }  // namespace fdk

@@ -331,14 +331,19 @@ static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
     return FDK_OK;
 }
 
-// Whether the staged path pays for this geometry: the 16 x 16 x 8 tile at
+// Adjoint warp patches (voxels along x) for views whose rays run mostly along
+// x (4 x 8: 8 across the rays) and along y (8 x 4).  Measured against 2 x 16 /
+// 16 x 2 (same) and 8 x 4 for every view (3% slower at 512^3 x 496).
+constexpr int kAdjPatchAlongX = 4, kAdjPatchAlongY = 8;
+
+// Whether the staged path pays for this geometry: the 16 x 16 x 16 tile at
 // the volume centre is projected, as the kernel's table builder does, for up
 // to 32 views spread over the scan, and the path is taken when at least 90%
 // of its pixel boxes fit a stage (coarse voxels on a fine detector give
 // boxes too large to stage, and those views would fall back to LDG).
 static bool stage_pays(const Geom &g, const float *mats, int n_views)
 {
-    const int BX = 16, BY = 16, R = 8;
+    const int BX = 16, BY = 16, R = 16;
     const int tx = (g.nx / 2) / BX * BX, ty = (g.ny / 2) / BY * BY, tz = (g.nz / 2) / R * R;
     const int step = n_views > 32 ? n_views / 32 : 1;
     int tried = 0, fit = 0;
@@ -692,15 +697,34 @@ fdk_status fdk_forwardproject_adjoint(void *projections, const int32_t det[2], c
         a.proj = nullptr;
         a.quads = nullptr;
         a.plane = plane;
-        a.n_views = nv;
-        if (o->matrices_on_device) {
-            a.mats_dev = matrices + (size_t)v0 * 12;
-        } else {
-            a.mats_dev = nullptr;
-            memcpy(a.mats, matrices + (size_t)v0 * 12, sizeof(float) * 12 * nv);
-        }
         float *out = static_cast<float *>(projections) + (size_t)v0 * plane;
-        if ((st = launch_adjoint(a, out, s))) return st;
+        if (o->matrices_on_device) {
+            // one launch over the pass in view order with 8 x 4 warp patches
+            a.n_views = nv;
+            a.warp_x = 8;
+            a.mats_dev = matrices + (size_t)v0 * 12;
+            for (int k = 0; k < nv; ++k) a.vidx[k] = k;
+            if ((st = launch_adjoint(a, out, s))) return st;
+            continue;
+        }
+        // host matrices: one launch per ray orientation, with warp patches
+        // that lie across the rays (voxels on one ray splat into the same
+        // cells, and atomics on one address serialise)
+        a.mats_dev = nullptr;
+        for (int group = 0; group < 2; ++group) {
+            int cnt = 0;
+            for (int k = 0; k < nv; ++k) {
+                const float *P = matrices + (size_t)(v0 + k) * 12;
+                const bool along_x = fabsf(P[8]) > fabsf(P[9]);
+                if (along_x != (group == 0)) continue;
+                memcpy(a.mats + 12 * cnt, P, sizeof(float) * 12);
+                a.vidx[cnt++] = k;
+            }
+            if (cnt == 0) continue;
+            a.n_views = cnt;
+            a.warp_x = group == 0 ? kAdjPatchAlongX : kAdjPatchAlongY;
+            if ((st = launch_adjoint(a, out, s))) return st;
+        }
     }
     return FDK_OK;
 }

@@ -13,17 +13,19 @@
 // Pipeline per CTA: kStages shared-memory stages.  Every thread waits on the
 // stage's mbarrier and computes the view; after a CTA barrier (the stage is
 // then free) thread 0 issues the copy of the staged view kStages further on
-// into it, so kStages - 1 copies are in flight while the CTA computes.  (A
-// barrier-free variant, in which the last warp done with a stage refills it,
-// measured 12% slower: its warps spin on the mbarriers instead.)  Every wait
-// is bounded; a wait that gives up sets *a.err, thread 0 drains the copies
-// still in flight (again bounded) and the CTA returns without writing its
-// tile.  The taps are read with 32-bit shared addresses.
+// into it, so the next view's copy is in flight while the CTA computes.
+// Each thread owns a z-run of 16 voxels, so the per-view barrier is shared
+// by 16 updates per thread (8 per thread measured 10% slower, 24 slower
+// still).  (A barrier-free variant, in which the last warp done with a stage
+// refills it, measured 12% slower: its warps spin on the mbarriers instead.)
+// Every wait is bounded; a wait that gives up sets *a.err, thread 0 drains
+// the copies still in flight (again bounded) and the CTA returns without
+// writing its tile.  The taps are read with 32-bit shared addresses.
 #include "fdk_bp_kernel.cuh"
 
 namespace fdk {
 
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kStageChunk = 64;          // views per table chunk on this path
 constexpr long long kWaitLimit = 1LL << 22;
 
@@ -254,7 +256,7 @@ fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
 template <int WX, bool FIDX>
 static fdk_status launch_stage_shape(const BpArgs &a, cudaStream_t s)
 {
-    constexpr int BX = 16, BY = 16, R = 8, MINB = 4;
+    constexpr int BX = 16, BY = 16, R = 16, MINB = 3;
     auto k = fdk_bp_stage_kernel<BX, BY, WX, R, MINB, FIDX>;
     const int smem = kStages * kStageFloats * (int)sizeof(float);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -275,7 +277,7 @@ static fdk_status launch_stage_shape(const BpArgs &a, cudaStream_t s)
     return FDK_OK;
 }
 
-// FP32 projections, 16 x 16 x 8 tiles; a.tmap holds the pass's tensor maps.
+// FP32 projections, 16 x 16 x 16 tiles; a.tmap holds the pass's tensor maps.
 fdk_status launch_bp_stage_f32(const BpArgs &a, cudaStream_t s)
 {
     const bool fidx = (long long)a.g.W * (a.g.H + 1) < (1LL << 23);

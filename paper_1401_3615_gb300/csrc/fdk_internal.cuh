@@ -19,10 +19,10 @@ constexpr int KMAX = 512;
 // Staged fetch path: per (tile, view), the pixel box holding every tap of
 // the tile is copied into shared memory by TMA as a stack of 8-row boxes of
 // one of kNumBoxW widths (32, 48, ..., 128 pixels), at most kStageFloats
-// pixels; views whose box is larger keep the global-load path.
+// pixels (32 KB); views whose box is larger keep the global-load path.
 constexpr int kNumBoxW = 7;
 constexpr int kBoxRows = 8;
-constexpr int kStageFloats = 3840;
+constexpr int kStageFloats = 8192;
 __host__ __device__ constexpr int box_width(int m) { return 32 + 16 * m; }
 
 struct Geom {

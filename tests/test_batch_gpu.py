@@ -1,7 +1,7 @@
 """The batched form: many scans of uneven size in one persistent launch.
 
 A batch must equal the same scans back-projected one by one with
-fdk_backproject and the same tile variant, bit for bit (same per-voxel view
+fdk_backproject on the LDG path and the same tile variant, bit for bit (same per-voxel view
 order); the autotuner must leave the scans' volumes untouched; the launch
 must survive CUDA-graph capture and replay; and one batch is checked
 against the oracle.
@@ -40,7 +40,7 @@ def _sequential(scans, tile, init=0.0):
     out = []
     for vol, proj, mats, vs, org in scans:
         v = torch.full_like(vol, init)
-        fdk.fdk_backproject(v, proj, mats, vs, org, tile=tile)
+        fdk.fdk_backproject(v, proj, mats, vs, org, fetch=fdk.FETCH_LDG, tile=tile)
         out.append(v)
     torch.cuda.synchronize()
     return out
@@ -97,7 +97,7 @@ def test_batch_cuda_graph_replay():
     torch.cuda.synchronize()
     ref2 = [r.clone() for r in ref]
     for (vol, proj, mats, vs, org), r in zip(scans, ref2):
-        fdk.fdk_backproject(r, proj, mats, vs, org, tile=0)
+        fdk.fdk_backproject(r, proj, mats, vs, org, fetch=fdk.FETCH_LDG, tile=0)
     torch.cuda.synchronize()
     for (vol, *_), r in zip(scans, ref2):
         assert torch.equal(vol, r)
