@@ -545,8 +545,13 @@ def run_batched(args):
         for vol, proj, mats, vs, org in scans:
             fdk.fdk_backproject(vol, proj, mats, vs, org, tile=plan.tile)
 
+    def sequential_default():
+        for vol, proj, mats, vs, org in scans:
+            fdk.fdk_backproject(vol, proj, mats, vs, org)
+
     plan = fdk.fdk_batch_plan_create(scans, autotune=True)
     ms_seq = timed(sequential, args.steps)
+    ms_seq_default = timed(sequential_default, args.steps)
     ms_batch = timed(plan.execute, args.steps)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
@@ -563,7 +568,11 @@ def run_batched(args):
                                "detectors 640x480..1248x960, FP32",
                    "updates_per_step": updates, "autotuned_tile": plan.tile,
                    "views_total": sum(c.n_views for c in cfgs)},
-        "sequential_plain_calls": {"ms_per_step": ms_seq, "value": updates / (ms_seq * 1e-3) / 1e9},
+        "sequential_plain_calls": {"ms_per_step": ms_seq, "value": updates / (ms_seq * 1e-3) / 1e9,
+                                   "what": "fdk_backproject per scan with the plan's tile (LDG path)"},
+        "sequential_default_calls": {"ms_per_step": ms_seq_default,
+                                     "value": updates / (ms_seq_default * 1e-3) / 1e9,
+                                     "what": "fdk_backproject per scan with default options (AUTO)"},
         "batch_plan_execute": {"ms_per_step": ms_batch, "value": updates / (ms_batch * 1e-3) / 1e9},
         "cuda_graph_replay": {"ms_per_step": ms_graph, "value": updates / (ms_graph * 1e-3) / 1e9},
     }

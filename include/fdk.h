@@ -247,9 +247,9 @@ typedef struct fdk_batch_plan_t *fdk_batch_plan;
  * descriptors, matrices and a (scan, tile) work list to device memory it
  * owns (synchronously, on the current device) and keeps the scans' device
  * pointers: the volumes and projections must stay allocated while the plan
- * is used.  With opts->autotune = 1 it times the tile variants 0 and 2..5
+ * is used.  With opts->autotune = 1 it times the tile variants 0, 2..5 and 7
  * on the batch (writing into a scratch volume, never into the scans'
- * volumes) and keeps the fastest; otherwise opts->tile (0..5) is used.
+ * volumes) and keeps the fastest; otherwise opts->tile (0..5 or 7) is used.
  * opts->proj_dtype must be FDK_F32 and opts->fetch AUTO or LDG.
  */
 FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans,

@@ -967,7 +967,7 @@ static fdk_status plan_autotune(fdk_batch_plan_t *p)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cands[] = {0, 2, 3, 4, 5};
+    const int cands[] = {0, 2, 3, 4, 5, 7};
     int best = 0;
     float best_ms = 3.0e38f;
     fdk_status st = FDK_OK;
@@ -1012,7 +1012,7 @@ fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, in
     if (o.fetch != FDK_FETCH_AUTO && o.fetch != FDK_FETCH_LDG)
         return fail(FDK_ERR_INVALID_ARG, "batches use the LDG fetch path");
     if (o.matrices_on_device) return fail(FDK_ERR_INVALID_ARG, "batches take host matrices");
-    if (o.tile > 5) return fail(FDK_ERR_INVALID_ARG, "batches take tile variants 0..5");
+    if (o.tile == 6 || o.tile > 7) return fail(FDK_ERR_INVALID_ARG, "batches take tile variants 0..5 and 7");
     if (n_scans < 1 || !scans) return fail(FDK_ERR_INVALID_ARG, "need at least one scan");
     std::unique_ptr<fdk_batch_plan_t> p(new fdk_batch_plan_t());
     cudaGetDevice(&p->dev);

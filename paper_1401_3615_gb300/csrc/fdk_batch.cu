@@ -82,6 +82,7 @@ static fdk_status launch_batched_fidx(const BatchLaunch &b, int tile, cudaStream
     case 3: return launch_batched_tile<3, FIDX>(b, s);
     case 4: return launch_batched_tile<4, FIDX>(b, s);
     case 5: return launch_batched_tile<5, FIDX>(b, s);
+    case 7: return launch_batched_tile<7, FIDX>(b, s);
     default: return launch_batched_tile<0, FIDX>(b, s);
     }
 }
