@@ -330,23 +330,20 @@ def _fft_len(W: int) -> int:
 
 
 def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
-    """End to end through the public API with host buffers: every step copies
-    the projections from pinned host memory to the device, back-projects
-    into a zeroed volume and reads the volume back to pinned host memory."""
+    """End to end through the C-ABI entry point for host buffers
+    (fdk_backproject_host): every step copies the volume and the projections
+    from pinned host memory to the device -- the projections in chunks of
+    views whose copies overlap the back-projection -- and the volume back."""
     import torch
     import torch.distributed as dist
     from paper_1401_3615_gb300 import fdk
     h_proj = torch.empty(proj.shape, dtype=proj.dtype, pin_memory=True)
     h_proj.copy_(proj)
-    h_vol = torch.empty(vol.shape, dtype=vol.dtype, pin_memory=True)
-    d_proj = torch.empty_like(proj)
+    h_vol = torch.zeros(vol.shape, dtype=vol.dtype, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 5))
 
     def e2e_step():
-        d_proj.copy_(h_proj, non_blocking=True)
-        vol.zero_()
-        fdk.fdk_backproject(vol, d_proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
-        h_vol.copy_(vol, non_blocking=True)
+        fdk.fdk_backproject_host(h_vol, h_proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -357,9 +354,12 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks((time.perf_counter() - w0) / e2e_steps, world, dev)
+    vol_bytes = int(vol.numel() * vol.element_size())
     return {"value": _job_rate(world, upd_full, e2e_s), "unit": UNIT,
-            "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
-            "d2h_bytes_per_step": int(vol.numel() * vol.element_size())}
+            "h2d_bytes_per_step": int(proj.numel() * proj.element_size()) + vol_bytes,
+            "d2h_bytes_per_step": vol_bytes, "ms_per_step": e2e_s * 1e3,
+            "how": "fdk_backproject_host on pinned host buffers (volume in, projections in 4 overlapped "
+                   "chunks, volume out), wall clock"}
 
 
 def run_ours(args):

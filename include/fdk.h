@@ -161,6 +161,32 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
 #define FDK_STATIC_QUAD_BYTES (64u * 1024u * 1024u)
 
 /*
+ * fdk_backproject_host -- fdk_backproject for buffers in HOST memory: volume
+ * (nz, ny, nx) FP32 is accumulated (+=), projections (n_views, H, W) in
+ * opts->proj_dtype, matrices row-major 3x4 (host; matrices_on_device must
+ * be 0).  Pinned (page-locked) buffers give overlapped copies; pageable ones
+ * work but copy synchronously.
+ *
+ * How: the volume is copied to the device, the projections follow in 1, 2
+ * or 4 chunks of views (n_views < 64, < 256, otherwise) through two device
+ * buffers on a copy stream, so the copy of one chunk overlaps the
+ * back-projection of the previous one (fdk_backproject on opts->stream, same
+ * fetch path and tile), and the volume is copied back.  The call
+ * synchronises opts->stream before it returns.  Each chunk is its own pass,
+ * so the per-voxel summation order differs from one fdk_backproject call
+ * over all views by FP32 rounding.
+ *
+ * Device buffers (the volume and two chunks) are cached per device and
+ * reused; fdk_release() frees them.  Calls are serialised by the library.
+ * Errors: as fdk_backproject; INVALID_ARG also for device buffers or device
+ * matrices.
+ */
+FDK_API fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const float voxel_size[3],
+                                        const float origin[3], const void *projections,
+                                        const int32_t det[2], const float *matrices, int32_t n_views,
+                                        const fdk_opts *opts);
+
+/*
  * fdk_backproject_static -- the same back-projection as fdk_backproject,
  * for callers that must not allocate device memory.  The paper has no
  * counterpart; this is a service of the library.
@@ -311,8 +337,9 @@ FDK_API fdk_status fdk_microbench(int32_t which, int32_t param, double *result);
 /* Message for the last non-OK status returned on this thread ("" if none). */
 FDK_API const char *fdk_last_error(void);
 
-/* Drop cached per-buffer state (texture objects) on all devices.  Call only
- * when no work that uses them is in flight. */
+/* Drop cached per-buffer state (texture arrays, staging buffers, spectra,
+ * host-path buffers) on all devices.  Call only when no work that uses them
+ * is in flight. */
 FDK_API void fdk_release(void);
 
 /* ABI version, currently 1. */

@@ -486,12 +486,15 @@ const char *fdk_last_error(void) { return g_err; }
 
 int32_t fdk_version(void) { return 1; }
 
+static void release_host_stages();
+
 void fdk_release(void)
 {
     release_textures();
     release_quads();
     release_spectra();
     release_err_words();
+    release_host_stages();
 }
 
 fdk_status fdk_device_status(void)
@@ -662,6 +665,166 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         }
     }
     if (guard) cudaEventRecord(guard, s);
+    return FDK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer entry point: per device a volume buffer and two projection
+// chunk buffers (grown on demand, reused), a copy stream and events.
+struct HostStage {
+    int dev = 0;
+    float *vol = nullptr;
+    size_t vol_bytes = 0;
+    void *chunk[2] = {nullptr, nullptr};
+    size_t chunk_bytes = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+};
+static std::mutex g_host_mu;
+static std::vector<std::unique_ptr<HostStage>> g_host;
+
+static void host_stage_free(HostStage *h)
+{
+    if (h->copy) cudaStreamSynchronize(h->copy);
+    cudaFree(h->vol);
+    cudaFree(h->chunk[0]);
+    cudaFree(h->chunk[1]);
+    for (int b = 0; b < 2; ++b) {
+        if (h->copied[b]) cudaEventDestroy(h->copied[b]);
+        if (h->consumed[b]) cudaEventDestroy(h->consumed[b]);
+    }
+    if (h->copy) cudaStreamDestroy(h->copy);
+    *h = HostStage();
+}
+
+static void release_host_stages()
+{
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &p : g_host) {
+        cudaSetDevice(p->dev);
+        cudaDeviceSynchronize();
+        host_stage_free(p.get());
+    }
+    g_host.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
+// Caller holds g_host_mu.
+static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, HostStage **out)
+{
+    HostStage *h = nullptr;
+    for (auto &p : g_host)
+        if (p->dev == dev) h = p.get();
+    if (!h) {
+        g_host.emplace_back(new HostStage());
+        h = g_host.back().get();
+        h->dev = dev;
+        if (cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FDK_ERR_CUDA, "copy stream creation failed");
+        }
+        for (int b = 0; b < 2; ++b)
+            if (cudaEventCreateWithFlags(&h->copied[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->consumed[b], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FDK_ERR_CUDA, "event creation failed");
+            }
+    }
+    if (h->vol_bytes < vol_bytes) {
+        cudaFree(h->vol);
+        h->vol = nullptr;
+        h->vol_bytes = 0;
+        if (cudaMalloc(&h->vol, vol_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FDK_ERR_OOM, "device volume allocation failed");
+        }
+        h->vol_bytes = vol_bytes;
+    }
+    if (h->chunk_bytes < chunk_bytes) {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(h->chunk[b]);
+            h->chunk[b] = nullptr;
+        }
+        h->chunk_bytes = 0;
+        for (int b = 0; b < 2; ++b)
+            if (cudaMalloc(&h->chunk[b], chunk_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FDK_ERR_OOM, "device projection chunk allocation failed");
+            }
+        h->chunk_bytes = chunk_bytes;
+    }
+    *out = h;
+    return FDK_OK;
+}
+
+fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const float voxel_size[3],
+                                const float origin[3], const void *projections, const int32_t det[2],
+                                const float *matrices, int32_t n_views, const fdk_opts *opts)
+{
+    g_err[0] = 0;
+    const fdk_opts *o = opts ? opts : &kDefaultOpts;
+    fdk_status st = check_opts(o);
+    if (st) return st;
+    if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
+    if (o->matrices_on_device) return fail(FDK_ERR_INVALID_ARG, "fdk_backproject_host takes host matrices");
+    Geom g;
+    if ((st = check_geometry(dims, voxel_size, origin, det, matrices, n_views, &g))) return st;
+    if (!volume) return fail(FDK_ERR_INVALID_ARG, "volume is null");
+    if (n_views > 0 && !projections) return fail(FDK_ERR_INVALID_ARG, "projections is null");
+    if ((st = check_alignment(volume, 4, "volume"))) return st;
+    if (n_views == 0) return FDK_OK;
+    const size_t esz = dtype_size(o->proj_dtype);
+    if ((st = check_alignment(projections, esz, "projections"))) return st;
+    if ((st = check_matrices(matrices, n_views, 0))) return st;
+    for (const void *p : {(const void *)volume, projections}) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+            cudaGetLastError();
+        } else if (attr.type == cudaMemoryTypeDevice) {
+            return fail(FDK_ERR_INVALID_ARG, "fdk_backproject_host takes host buffers (use fdk_backproject)");
+        }
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t plane = (size_t)g.W * g.H;
+    const size_t vol_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
+    // chunks of views: the copy of one overlaps the back-projection of the last
+    const int nchunks = n_views >= 256 ? 4 : (n_views >= 64 ? 2 : 1);
+    const int C = (n_views + nchunks - 1) / nchunks;
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    HostStage *h = nullptr;
+    if ((st = host_stage_get(dev, vol_bytes, (size_t)C * plane * esz, &h))) return st;
+    cudaStream_t s = (cudaStream_t)o->stream;
+    fdk_opts oc = *o;
+    oc.stream = s;
+    cudaError_t e = cudaMemcpyAsync(h->vol, volume, vol_bytes, cudaMemcpyHostToDevice, s);
+    for (int c = 0; e == cudaSuccess && st == FDK_OK && c * C < n_views; ++c) {
+        const int b = c & 1, v0 = c * C;
+        const int nv = (n_views - v0 < C) ? n_views - v0 : C;
+        if (c >= 2) e = cudaStreamWaitEvent(h->copy, h->consumed[b], 0);   // buffer b is free
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->chunk[b], static_cast<const char *>(projections) + (size_t)v0 * plane * esz,
+                                (size_t)nv * plane * esz, cudaMemcpyHostToDevice, h->copy);
+        if (e == cudaSuccess) e = cudaEventRecord(h->copied[b], h->copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->copied[b], 0);
+        if (e != cudaSuccess) break;
+        st = fdk_backproject(h->vol, dims, voxel_size, origin, h->chunk[b], det, matrices + (size_t)v0 * 12, nv,
+                             &oc);
+        if (st == FDK_OK) e = cudaEventRecord(h->consumed[b], s);
+    }
+    if (e == cudaSuccess && st == FDK_OK) e = cudaMemcpyAsync(volume, h->vol, vol_bytes, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamSynchronize(h->copy);
+    if (st) return st;
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("host back-projection: %s", cudaGetErrorString(e));
+        return FDK_ERR_CUDA;
+    }
     return FDK_OK;
 }
 

@@ -69,6 +69,8 @@ def _load():
             lib.fdk_forwardproject_adjoint.argtypes = [vp, i3, vp, i3, f3, f3, vp, ctypes.c_int32, op]
             lib.fdk_backproject_static.argtypes = [vp, i3, f3, f3, vp, i3, vp, ctypes.c_int32, op]
             lib.fdk_backproject_static.restype = ctypes.c_int
+            lib.fdk_backproject_host.argtypes = [vp, i3, f3, f3, vp, i3, vp, ctypes.c_int32, op]
+            lib.fdk_backproject_host.restype = ctypes.c_int
             lib.fdk_count_updates.argtypes = [ctypes.POINTER(ctypes.c_int64), i3, f3, f3, i3, vp,
                                               ctypes.c_int32, op]
             for fn in (lib.fdk_backproject, lib.fdk_forwardproject_adjoint, lib.fdk_count_updates):
@@ -192,6 +194,35 @@ def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, v
     st = lib.fdk_backproject(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
                              _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
                              ctypes.byref(o))
+    _check(st)
+    return volume
+
+
+def fdk_backproject_host(volume: torch.Tensor, projections: torch.Tensor, matrices, voxel_size, origin,
+                         *, fetch: int = FETCH_AUTO, tile: int = 0, stream=None) -> torch.Tensor:
+    """fdk_backproject for host (CPU) tensors: volume[nz,ny,nx] FP32 +=
+    back-projection of projections[n,H,W] (FP32/BF16/FP16), host matrices.
+    The library copies in chunks of views, overlapping copies with the
+    back-projection (pinned tensors overlap; pageable ones copy
+    synchronously), and synchronises before returning.  Returns ``volume``."""
+    if volume.is_cuda or projections.is_cuda:
+        raise ValueError("fdk_backproject_host takes host tensors (use fdk_backproject for CUDA tensors)")
+    if volume.dtype != torch.float32 or volume.dim() != 3 or not volume.is_contiguous():
+        raise ValueError("volume must be a contiguous float32 (nz, ny, nx) tensor")
+    if projections.dim() != 3 or not projections.is_contiguous():
+        raise ValueError("projections must be a contiguous (n_views, H, W) tensor")
+    if projections.dtype not in _DTYPES:
+        raise ValueError(f"unsupported projection dtype {projections.dtype}")
+    n = projections.shape[0]
+    m, mptr, mdev = _mats(matrices, n)
+    if mdev:
+        raise ValueError("fdk_backproject_host takes host matrices")
+    nz, ny, nx = volume.shape
+    vs, org = _geom(voxel_size, origin)
+    o = _opts(_DTYPES[projections.dtype], False, stream, fetch, tile)
+    st = _load().fdk_backproject_host(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
+                                      _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
+                                      ctypes.byref(o))
     _check(st)
     return volume
 
