@@ -546,6 +546,13 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     if (n_views == 0) return FDK_OK;
     if ((st = check_alignment(projections, dtype_size(o->proj_dtype), "projections"))) return st;
     if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
+    if (o->fetch == FDK_FETCH_STAGE) {
+        // the staged path's own requirements, checked before any CUDA call
+        if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_UNSUPPORTED, "the staged path takes FP32 projections");
+        if (o->tile != 0) return fail(FDK_ERR_INVALID_ARG, "the staged path uses tile 0");
+        if (g.W % 4 != 0 || ((uintptr_t)projections) % 16 != 0)
+            return fail(FDK_ERR_UNSUPPORTED, "the staged path needs W % 4 == 0 and 16-byte aligned projections");
+    }
     if ((st = check_device_ptr(volume, "volume"))) return st;
     if ((st = check_device_ptr(projections, "projections"))) return st;
     if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
@@ -574,10 +581,6 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     bool use_stage = false;
     a.err = nullptr;
     if (want == FDK_FETCH_STAGE) {
-        if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_UNSUPPORTED, "the staged path takes FP32 projections");
-        if (o->tile != 0) return fail(FDK_ERR_INVALID_ARG, "the staged path uses tile 0");
-        if (g.W % 4 != 0 || ((uintptr_t)projections) % 16 != 0)
-            return fail(FDK_ERR_UNSUPPORTED, "the staged path needs W % 4 == 0 and 16-byte aligned projections");
         if (!tmap_encoder()) return fail(FDK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
         if ((st = err_word(dev, &a.err))) return st;
         use_stage = true;

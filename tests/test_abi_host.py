@@ -101,3 +101,49 @@ def test_misaligned_pointer_rejected():
 def test_zero_views_is_noop_without_gpu():
     assert _call_bp(n=0, proj=0, mats=None) == fdk.FDK_OK
     assert fdk.fdk_last_error() == ""
+
+
+def test_host_entry_point_validates_before_cuda():
+    """fdk_backproject_host shares the argument checks of fdk_backproject
+    and refuses device matrices, all before any CUDA call."""
+    lib = _raw()
+    d = (ctypes.c_int32 * 3)(4, 4, 4)
+    f3 = (ctypes.c_float * 3)(1, 1, 1)
+    m = (ctypes.c_float * 12)(*([1.0] * 12))
+    det = (ctypes.c_int32 * 2)(8, 8)
+    st = lib.fdk_backproject_host(None, d, f3, f3, ctypes.c_void_p(256), det, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "volume" in fdk.fdk_last_error()
+    o = fdk.fdk_opts()
+    o.matrices_on_device = 1
+    st = lib.fdk_backproject_host(ctypes.c_void_p(256), d, f3, f3, ctypes.c_void_p(256), det, m, 1,
+                                  ctypes.byref(o))
+    assert st == fdk.FDK_ERR_INVALID_ARG and "host matrices" in fdk.fdk_last_error()
+    bad = (ctypes.c_int32 * 3)(4, 0, 4)
+    st = lib.fdk_backproject_host(ctypes.c_void_p(256), bad, f3, f3, ctypes.c_void_p(256), det, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "dims" in fdk.fdk_last_error()
+    assert lib.fdk_backproject_host(ctypes.c_void_p(256), d, f3, f3, None, det, m, 0, None) == fdk.FDK_OK
+
+
+def test_microbench_validates_before_cuda():
+    lib = _raw()
+    out = ctypes.c_double(0.0)
+    for which, param, msg in [(fdk.MICRO_LDG, 3, "divide 32"), (fdk.MICRO_LDS, 0, "divide 32"),
+                              (fdk.MICRO_TLD4, 1, "texture size"), (fdk.MICRO_CHASE, 0, "ring"),
+                              (42, 1, "unknown")]:
+        assert lib.fdk_microbench(which, param, ctypes.byref(out)) == fdk.FDK_ERR_INVALID_ARG
+        assert msg in fdk.fdk_last_error()
+    assert lib.fdk_microbench(fdk.MICRO_RCP, 0, None) == fdk.FDK_ERR_INVALID_ARG
+
+
+def test_staged_fetch_checks_before_cuda():
+    """The staged path's own requirements are checked on the host: FP32 only,
+    tile 0 only, W a multiple of 4 and a 16-byte aligned image base."""
+    for field, val, kw, msg in [("proj_dtype", fdk.FDK_BF16, {}, "FP32"),
+                                ("tile", 2, {}, "tile 0"),
+                                (None, None, dict(det=(10, 8)), "W % 4")]:
+        o = fdk.fdk_opts()
+        o.fetch = fdk.FETCH_STAGE
+        if field:
+            setattr(o, field, val)
+        st = _call_bp(opts=o, **kw)
+        assert st != fdk.FDK_OK and msg in fdk.fdk_last_error(), (field, fdk.fdk_last_error())
