@@ -103,7 +103,10 @@ typedef struct fdk_opts {
                                     5: 16x16, 4   6: 32x8, 16   7: 16x16, 16 */
     int32_t autotune;            /* fdk_batch_plan_create only: 1 = time the tile variants on
                                     the batch and keep the fastest; elsewhere must be 0 */
-    int32_t reserved[9];         /* must be zero */
+    int32_t overwrite;           /* fdk_backproject_host only: 1 = the result replaces the host
+                                    volume (the device copy starts at zero, so the volume is not
+                                    copied in); 0 = accumulate (+=); elsewhere must be 0 */
+    int32_t reserved[8];         /* must be zero */
 } fdk_opts;
 
 /*
@@ -162,12 +165,14 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
 
 /*
  * fdk_backproject_host -- fdk_backproject for buffers in HOST memory: volume
- * (nz, ny, nx) FP32 is accumulated (+=), projections (n_views, H, W) in
+ * (nz, ny, nx) FP32 is accumulated (+=), or replaced with opts->overwrite = 1
+ * (then it is not copied to the device, whose copy starts at zero),
+ * projections (n_views, H, W) in
  * opts->proj_dtype, matrices row-major 3x4 (host; matrices_on_device must
  * be 0).  Pinned (page-locked) buffers give overlapped copies; pageable ones
  * work but copy synchronously.
  *
- * How: the volume is copied to the device, the projections follow in 1, 2
+ * How: the volume is copied to the device (or zeroed there), the projections follow in 1, 2
  * or 4 chunks of views (n_views < 64, < 256, otherwise) through two device
  * buffers on a copy stream, so the copy of one chunk overlaps the
  * back-projection of the previous one (fdk_backproject on opts->stream, same

@@ -30,7 +30,7 @@ static fdk_status fail(fdk_status st, const char *msg)
     return st;
 }
 
-static const fdk_opts kDefaultOpts = {FDK_F32, 0, nullptr, FDK_FETCH_AUTO, 0, 0, {0}};
+static const fdk_opts kDefaultOpts = {FDK_F32, 0, nullptr, FDK_FETCH_AUTO, 0, 0, 0, {0}};
 
 // Shared checks for the geometry arguments of every entry point.
 static fdk_status check_geometry(const int32_t dims[3], const float voxel_size[3],
@@ -62,8 +62,10 @@ static fdk_status check_geometry(const int32_t dims[3], const float voxel_size[3
     return FDK_OK;
 }
 
-static fdk_status check_opts(const fdk_opts *o)
+static fdk_status check_opts(const fdk_opts *o, bool allow_overwrite = false)
 {
+    if (o->overwrite && !allow_overwrite)
+        return fail(FDK_ERR_INVALID_ARG, "overwrite applies to fdk_backproject_host only");
     if (o->proj_dtype != FDK_F32 && o->proj_dtype != FDK_BF16 && o->proj_dtype != FDK_F16)
         return fail(FDK_ERR_INVALID_ARG, "unknown proj_dtype");
     if (o->matrices_on_device != 0 && o->matrices_on_device != 1)
@@ -72,7 +74,8 @@ static fdk_status check_opts(const fdk_opts *o)
         return fail(FDK_ERR_INVALID_ARG, "unknown fetch path");
     if (o->tile < 0 || o->tile > 7) return fail(FDK_ERR_INVALID_ARG, "tile must be 0..7");
     if (o->autotune != 0 && o->autotune != 1) return fail(FDK_ERR_INVALID_ARG, "autotune must be 0 or 1");
-    for (int q = 0; q < 9; ++q)
+    if (o->overwrite != 0 && o->overwrite != 1) return fail(FDK_ERR_INVALID_ARG, "overwrite must be 0 or 1");
+    for (int q = 0; q < 8; ++q)
         if (o->reserved[q] != 0) return fail(FDK_ERR_INVALID_ARG, "reserved option fields must be zero");
     return FDK_OK;
 }
@@ -769,7 +772,7 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
 {
     g_err[0] = 0;
     const fdk_opts *o = opts ? opts : &kDefaultOpts;
-    fdk_status st = check_opts(o);
+    fdk_status st = check_opts(o, true);
     if (st) return st;
     if (o->autotune) return fail(FDK_ERR_INVALID_ARG, "autotune applies to fdk_batch_plan_create only");
     if (o->matrices_on_device) return fail(FDK_ERR_INVALID_ARG, "fdk_backproject_host takes host matrices");
@@ -803,7 +806,9 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
     cudaStream_t s = (cudaStream_t)o->stream;
     fdk_opts oc = *o;
     oc.stream = s;
-    cudaError_t e = cudaMemcpyAsync(h->vol, volume, vol_bytes, cudaMemcpyHostToDevice, s);
+    oc.overwrite = 0;
+    cudaError_t e = o->overwrite ? cudaMemsetAsync(h->vol, 0, vol_bytes, s)
+                                 : cudaMemcpyAsync(h->vol, volume, vol_bytes, cudaMemcpyHostToDevice, s);
     for (int c = 0; e == cudaSuccess && st == FDK_OK && c * C < n_views; ++c) {
         const int b = c & 1, v0 = c * C;
         const int nv = (n_views - v0 < C) ? n_views - v0 : C;

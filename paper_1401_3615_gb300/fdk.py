@@ -33,7 +33,7 @@ class FdkError(RuntimeError):
 class fdk_opts(ctypes.Structure):
     _fields_ = [("proj_dtype", ctypes.c_int32), ("matrices_on_device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("fetch", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("autotune", ctypes.c_int32), ("overwrite", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class fdk_scan(ctypes.Structure):
@@ -199,12 +199,15 @@ def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, v
 
 
 def fdk_backproject_host(volume: torch.Tensor, projections: torch.Tensor, matrices, voxel_size, origin,
-                         *, fetch: int = FETCH_AUTO, tile: int = 0, stream=None) -> torch.Tensor:
+                         *, fetch: int = FETCH_AUTO, tile: int = 0, stream=None,
+                         overwrite: bool = False) -> torch.Tensor:
     """fdk_backproject for host (CPU) tensors: volume[nz,ny,nx] FP32 +=
     back-projection of projections[n,H,W] (FP32/BF16/FP16), host matrices.
     The library copies in chunks of views, overlapping copies with the
     back-projection (pinned tensors overlap; pageable ones copy
-    synchronously), and synchronises before returning.  Returns ``volume``."""
+    synchronously), and synchronises before returning.  With
+    ``overwrite=True`` the result replaces ``volume`` (which is then not
+    copied to the device).  Returns ``volume``."""
     if volume.is_cuda or projections.is_cuda:
         raise ValueError("fdk_backproject_host takes host tensors (use fdk_backproject for CUDA tensors)")
     if volume.dtype != torch.float32 or volume.dim() != 3 or not volume.is_contiguous():
@@ -220,6 +223,7 @@ def fdk_backproject_host(volume: torch.Tensor, projections: torch.Tensor, matric
     nz, ny, nx = volume.shape
     vs, org = _geom(voxel_size, origin)
     o = _opts(_DTYPES[projections.dtype], False, stream, fetch, tile)
+    o.overwrite = 1 if overwrite else 0
     st = _load().fdk_backproject_host(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
                                       _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
                                       ctypes.byref(o))

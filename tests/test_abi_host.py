@@ -80,6 +80,9 @@ def test_bad_options_rejected():
     o = fdk.fdk_opts()
     o.reserved[3] = 1
     assert _call_bp(opts=o) == fdk.FDK_ERR_INVALID_ARG
+    o = fdk.fdk_opts()
+    o.overwrite = 1                      # only fdk_backproject_host takes it
+    assert _call_bp(opts=o) == fdk.FDK_ERR_INVALID_ARG and "overwrite" in fdk.fdk_last_error()
 
 
 def test_nonfinite_matrix_rejected():

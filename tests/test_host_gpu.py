@@ -54,6 +54,15 @@ def test_four_chunks_accumulate_against_oracle(pinned):
     assert_parity(2 * ref + 0.5, vol.numpy().astype(np.float64), what=f"pinned={pinned}")
 
 
+def test_overwrite_replaces_the_host_volume():
+    s = synth.make_scan(synth.preset("small", n_views=300, det_w=40, det_h=32, nx=20, ny=18, nz=10))
+    ref = _oracle(s)
+    vol = torch.full(_shape(s), 7.0).pin_memory()
+    fdk.fdk_backproject_host(vol, s["proj"].float().contiguous().pin_memory(), s["mats"], s["voxel_size"],
+                             s["origin"], overwrite=True)
+    assert_parity(ref, vol.numpy().astype(np.float64), what="overwrite")
+
+
 def test_full_128_cube_496_views_and_half_storage():
     s = synth.make_scan(synth.PRESETS["fdk128"], device="cuda")
     ref = _oracle(s)
