@@ -472,6 +472,17 @@ def run_ours(args):
                     "achieved_full_count": upd_full / passes / (mean_launch * 1e-3) / 1e9}
         if clk.get("sm_mhz"):
             roofline["peak_at_measured_clock"] = peak_gups * clk["sm_mhz"] / sm_max
+        # the other ceilings, in the same clipped updates: HBM at the algorithmic bytes of a step
+        # (the volume read and written once per launch, every view read once)
+        alg_bytes = passes * 2 * vol.numel() * 4 + proj.numel() * proj.element_size()
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roofline["ceilings"] = {
+            "issue_gups": peak_gups,
+            "hbm_measured_gups": hbm * 1e9 / (alg_bytes / upd_clip) / 1e9,
+            "hbm_nominal_gups": 7900.0 * 1e9 / (alg_bytes / upd_clip) / 1e9,
+            "algorithmic_bytes_per_step": alg_bytes,
+            "binding": "issue",
+        }
         cpu = None
         if world == 1 and not args.no_cpu:
             import oracle
