@@ -164,7 +164,8 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
 #define FDK_STATIC_QUAD_BYTES (64u * 1024u * 1024u)
 
 /*
- * fdk_backproject_host -- fdk_backproject for buffers in HOST memory: volume
+ * fdk_backproject_host -- the back-projection of fdk_backproject (Listing 1,
+ * Sec. IV) for buffers in HOST memory: volume
  * (nz, ny, nx) FP32 is accumulated (+=), or replaced with opts->overwrite = 1
  * (then it is not copied to the device, whose copy starts at zero),
  * projections (n_views, H, W) in
