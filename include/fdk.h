@@ -165,13 +165,12 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
 
 /*
  * fdk_backproject_host -- the back-projection of fdk_backproject (Listing 1,
- * Sec. IV) for buffers in HOST memory: volume
- * (nz, ny, nx) FP32 is accumulated (+=), or replaced with opts->overwrite = 1
- * (then it is not copied to the device, whose copy starts at zero),
- * projections (n_views, H, W) in
- * opts->proj_dtype, matrices row-major 3x4 (host; matrices_on_device must
- * be 0).  Pinned (page-locked) buffers give overlapped copies; pageable ones
- * work but copy synchronously.
+ * Sec. IV) for buffers in HOST memory.  volume (nz, ny, nx) FP32 is
+ * accumulated (+=), or replaced with opts->overwrite = 1 (then it is not
+ * copied to the device, whose copy starts at zero); projections
+ * (n_views, H, W) in opts->proj_dtype; matrices row-major 3x4 in host memory
+ * (matrices_on_device must be 0).  Pinned (page-locked) buffers give
+ * overlapped copies; pageable ones work but copy synchronously.
  *
  * How: the volume is copied to the device (or zeroed there), the projections follow in 1, 2
  * or 4 chunks of views (n_views < 64, < 256, otherwise) through two device
