@@ -172,9 +172,10 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
  * (matrices_on_device must be 0).  Pinned (page-locked) buffers give
  * overlapped copies; pageable ones work but copy synchronously.
  *
- * How: the volume is copied to the device (or zeroed there), the projections follow in 1, 2
- * or 4 chunks of views (n_views < 64, < 256, otherwise) through two device
- * buffers on a copy stream, so the copy of one chunk overlaps the
+ * How: the volume is copied to the device (or zeroed there), the
+ * projections follow in 1, 2 or 4 chunks of views (n_views < 64, < 256,
+ * otherwise) through two device buffers on a copy stream, so the copy of one
+ * chunk overlaps the
  * back-projection of the previous one (fdk_backproject on opts->stream, same
  * fetch path and tile), and the volume is copied back.  The call
  * synchronises opts->stream before it returns.  Each chunk is its own pass,
