@@ -22,7 +22,7 @@
 
 namespace fdk {
 
-constexpr int kAdjBX = 16, kAdjBY = 16, kAdjR = 8, kAdjChunk = 64;
+constexpr int kAdjBX = 16, kAdjBY = 16, kAdjChunk = 64;
 constexpr int kAdjCap = 16384;  // cells of the shared footprint buffer (64 KB, dynamic)
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
@@ -246,13 +246,13 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     }
 }
 
-template <int WX>
+template <int R, int WX>
 static fdk_status launch_adjoint_wx(const BpArgs &a, float *proj_out, cudaStream_t s)
 {
-    dim3 grid((a.g.nx + kAdjBX - 1) / kAdjBX, (a.g.ny + kAdjBY - 1) / kAdjBY, (a.g.nz + kAdjR - 1) / kAdjR);
+    dim3 grid((a.g.nx + kAdjBX - 1) / kAdjBX, (a.g.ny + kAdjBY - 1) / kAdjBY, (a.g.nz + R - 1) / R);
     const bool vec4 = (a.g.W % 4) == 0 && ((uintptr_t)proj_out % 16) == 0;
     const size_t smem = (size_t)kAdjCap * sizeof(int);
-    auto k = vec4 ? fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, WX, true> : fdk_adj_kernel<kAdjBX, kAdjBY, kAdjR, WX, false>;
+    auto k = vec4 ? fdk_adj_kernel<kAdjBX, kAdjBY, R, WX, true> : fdk_adj_kernel<kAdjBX, kAdjBY, R, WX, false>;
     // opt in to more than 48 KB of dynamic shared memory (idempotent)
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) {
@@ -269,15 +269,22 @@ static fdk_status launch_adjoint_wx(const BpArgs &a, float *proj_out, cudaStream
     return FDK_OK;
 }
 
-// Warp patches of a.warp_x voxels along x by 32 / a.warp_x along y.
-fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t s)
+template <int R>
+static fdk_status launch_adjoint_r(const BpArgs &a, float *proj_out, cudaStream_t s)
 {
     switch (a.warp_x) {
-    case 2: return launch_adjoint_wx<2>(a, proj_out, s);
-    case 4: return launch_adjoint_wx<4>(a, proj_out, s);
-    case 16: return launch_adjoint_wx<16>(a, proj_out, s);
-    default: return launch_adjoint_wx<8>(a, proj_out, s);
+    case 2: return launch_adjoint_wx<R, 2>(a, proj_out, s);
+    case 4: return launch_adjoint_wx<R, 4>(a, proj_out, s);
+    case 16: return launch_adjoint_wx<R, 16>(a, proj_out, s);
+    default: return launch_adjoint_wx<R, 8>(a, proj_out, s);
     }
+}
+
+// Warp patches of a.warp_x voxels along x by 32 / a.warp_x along y; tiles of
+// 16 x 16 x z_run voxels, z_run 8 or 16.
+fdk_status launch_adjoint(const BpArgs &a, float *proj_out, int z_run, cudaStream_t s)
+{
+    return z_run == 16 ? launch_adjoint_r<16>(a, proj_out, s) : launch_adjoint_r<8>(a, proj_out, s);
 }
 
 }  // namespace fdk

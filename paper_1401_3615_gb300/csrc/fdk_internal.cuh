@@ -110,7 +110,7 @@ void batched_tile_dims(int tile, int *bx, int *by, int *r);
 size_t quad_elem_size(int dtype);
 fdk_status launch_make_quads(const void *proj, void *quads, int n, int W, int H, int dtype,
                              cudaStream_t stream);
-fdk_status launch_adjoint(const BpArgs &a, float *proj_out, cudaStream_t stream);
+fdk_status launch_adjoint(const BpArgs &a, float *proj_out, int z_run, cudaStream_t stream);
 fdk_status launch_count(const BpArgs &a, unsigned long long *count_dev, cudaStream_t stream);
 
 }  // namespace fdk

@@ -101,6 +101,22 @@ def test_adjoint_full_detector_sampled_views():
     assert_parity(ref, got, what="adjoint 256^3")
 
 
+def test_adjoint_fine_voxels_16_voxel_run():
+    """0.5 mm voxels on the 1248 x 960 detector (the 512^3 workload's pitch),
+    a 96 x 96 x 40 centre block, 32 views spread over the scan: the volume
+    stays far from the source and the footprints fit half the shared buffer,
+    so the adjoint takes its 16-voxel z-run; 40 slices leave a ragged last
+    run of 8."""
+    cfg = synth.preset("fdk512", nx=96, ny=96, nz=40)
+    geo = synth.geometry(cfg)
+    pick = np.linspace(0, cfg.n_views - 1, 32).astype(int)
+    dims, vs, org = synth.volume_geometry(cfg)
+    s = {"cfg": cfg, "mats": geo["mats"][pick], "dims": dims, "voxel_size": vs, "origin": org}
+    x = synth.gaussian_volume(dims, seed=36)
+    got = _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert_parity(_oracle_adj(s, x), got, what="adjoint 0.5 mm, 16-voxel run")
+
+
 def test_dot_product_identity(ragged):
     n, H, W = ragged["proj"].shape
     y = torch.from_numpy(synth.gaussian_projections(n, H, W, seed=41)).cuda()
