@@ -172,15 +172,26 @@ FDK_API fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], cons
  * (matrices_on_device must be 0).  Pinned (page-locked) buffers give
  * overlapped copies; pageable ones work but copy synchronously.
  *
- * How: the volume is copied to the device (or zeroed there), the
- * projections follow in 1, 2 or 4 chunks of views (n_views < 64, < 256,
- * otherwise) through two device buffers on a copy stream, so the copy of one
- * chunk overlaps the
- * back-projection of the previous one (fdk_backproject on opts->stream, same
- * fetch path and tile), and the volume is copied back.  The call
+ * How: the volume is copied to the device (or zeroed there).  The
+ * projections follow in chunks of views through two device buffers on a copy
+ * stream, so the copy of one chunk overlaps the back-projection of the
+ * previous one (fdk_backproject on opts->stream, same fetch path and tile;
+ * FDK_FETCH_AUTO is resolved once per chunk for the whole volume).
+ *   - n_views < 64: one chunk;
+ *   - from 64: chunks double in size from max(8, ceil(n/16)) views, and a
+ *     chunk takes every remaining view once fewer than twice its size
+ *     remain (31, 62, 124 and 279 views for 496), so back-projection starts
+ *     after a short copy and each copy hides under the previous chunk's
+ *     back-projection.
+ * The volume is copied back at the end.  With nz >= 64 the last chunk runs
+ * instead as up to 4 z-slabs of whole 16-voxel layers, each copied back
+ * while the next is back-projected.  This applies only where every slab
+ * origin (origin z + z0 * voxel z) is exact in FP32, and not with
+ * FDK_FETCH_TEX or FDK_FETCH_QUAD.  Each voxel then keeps its world position
+ * and its tile, so the result is the same as without slabs.  The call
  * synchronises opts->stream before it returns.  Each chunk is its own pass,
  * so the per-voxel summation order differs from one fdk_backproject call
- * over all views by FP32 rounding.
+ * over all views by FP32 rounding; with one chunk the results are equal.
  *
  * Device buffers (the volume and two chunks) are cached per device and
  * reused; fdk_release() frees them.  Calls are serialised by the library.

@@ -434,6 +434,16 @@ static bool stage_pays(const Geom &g, const float *mats, int n_views)
     return tried > 0 && fit * 10 >= tried * 9;
 }
 
+// What FDK_FETCH_AUTO resolves to the staged path for: FP32, tile 0, rows of
+// a multiple of 16 bytes, 16-byte aligned images, host matrices, and a
+// geometry for which staging pays.
+static bool auto_takes_stage(const Geom &g, const void *projections, const float *matrices, int n_views,
+                             const fdk_opts *o)
+{
+    return o->proj_dtype == FDK_F32 && o->tile == 0 && g.W % 4 == 0 && ((uintptr_t)projections) % 16 == 0 &&
+           !o->matrices_on_device && tmap_encoder() && stage_pays(g, matrices, n_views);
+}
+
 // One device word per device, set by a bounded wait that gave up.
 static std::mutex g_errw_mu;
 static std::vector<std::pair<int, unsigned *>> g_errw;
@@ -628,9 +638,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     // measures faster on GB300 there.  LDG elsewhere.  The texture and
     // quad paths only on request: both measure slower than LDG.
     int want = o->fetch;
-    if (want == FDK_FETCH_AUTO && o->proj_dtype == FDK_F32 && o->tile == 0 && g.W % 4 == 0 &&
-        ((uintptr_t)projections) % 16 == 0 && !o->matrices_on_device && tmap_encoder() &&
-        stage_pays(g, matrices, n_views))
+    if (want == FDK_FETCH_AUTO && auto_takes_stage(g, projections, matrices, n_views, o))
         want = FDK_FETCH_STAGE;
     bool use_tex = false, use_quad = false;
     TexStage *stage = nullptr;
@@ -742,7 +750,9 @@ struct HostStage {
     size_t chunk_bytes = 0;
     cudaStream_t copy = nullptr;
     cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    cudaEvent_t slab_done[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+constexpr int kHostSlabs = 4;
 static std::mutex g_host_mu;
 static std::vector<std::unique_ptr<HostStage>> g_host;
 
@@ -756,6 +766,8 @@ static void host_stage_free(HostStage *h)
         if (h->copied[b]) cudaEventDestroy(h->copied[b]);
         if (h->consumed[b]) cudaEventDestroy(h->consumed[b]);
     }
+    for (cudaEvent_t ev : h->slab_done)
+        if (ev) cudaEventDestroy(ev);
     if (h->copy) cudaStreamDestroy(h->copy);
     *h = HostStage();
 }
@@ -792,6 +804,11 @@ static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, 
         for (int b = 0; b < 2; ++b)
             if (cudaEventCreateWithFlags(&h->copied[b], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->consumed[b], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FDK_ERR_CUDA, "event creation failed");
+            }
+        for (cudaEvent_t &ev : h->slab_done)
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(FDK_ERR_CUDA, "event creation failed");
             }
@@ -854,9 +871,40 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
     cudaGetDevice(&dev);
     const size_t plane = (size_t)g.W * g.H;
     const size_t vol_bytes = (size_t)g.nx * g.ny * g.nz * sizeof(float);
-    // chunks of views: the copy of one overlaps the back-projection of the last
-    const int nchunks = n_views >= 256 ? 4 : (n_views >= 64 ? 2 : 1);
-    const int C = (n_views + nchunks - 1) / nchunks;
+    // Chunks of views through two device buffers: the copy of one overlaps
+    // the back-projection of the one before.  From 64 views on, the chunks
+    // double in size from max(8, ceil(n/16)) views, and a chunk takes every
+    // remaining view once fewer than twice its size remain.  So the
+    // back-projection starts after a short copy, and each chunk's copy hides
+    // under the back-projection of the chunk before it, half as large, while
+    // the host link moves a view in less than half the time a view's
+    // back-projection takes.  Every extra chunk costs a pass over the volume
+    // (about 0.6 ms at 512^3), so there are few: 31, 62, 124 and 279 views
+    // for 496.
+    std::vector<int> sizes;
+    if (n_views >= 64) {
+        int next = std::max(8, (n_views + 15) / 16), rem = n_views;
+        while (rem > 0) {
+            const int take = (rem < 2 * next) ? rem : next;
+            sizes.push_back(take);
+            rem -= take;
+            next *= 2;
+        }
+    } else {
+        sizes = {n_views};
+    }
+    const int C = *std::max_element(sizes.begin(), sizes.end());
+    // The last chunk runs as z-slabs of whole 16-voxel tile layers, each
+    // copied back while the next is back-projected, when nz >= 64 and every
+    // slab origin is exact in FP32 (each voxel keeps its world position and
+    // its tile, so the slabs compute what one call over the volume does).
+    const int slab_z = ((g.nz + kHostSlabs - 1) / kHostSlabs + 15) / 16 * 16;
+    bool slabs = g.nz >= 64 && (o->fetch == FDK_FETCH_AUTO || o->fetch == FDK_FETCH_LDG ||
+                                o->fetch == FDK_FETCH_STAGE);   // TEX and QUAD would re-stage per slab
+    for (int z0 = slab_z; slabs && z0 < g.nz; z0 += slab_z) {
+        const double zo = (double)origin[2] + (double)z0 * (double)voxel_size[2];
+        slabs = (double)(float)zo == zo;
+    }
     std::lock_guard<std::mutex> lk(g_host_mu);
     HostStage *h = nullptr;
     if ((st = host_stage_get(dev, vol_bytes, (size_t)C * plane * esz, &h))) return st;
@@ -864,11 +912,12 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
     fdk_opts oc = *o;
     oc.stream = s;
     oc.overwrite = 0;
+    const size_t slice = (size_t)g.nx * g.ny;
     cudaError_t e = o->overwrite ? cudaMemsetAsync(h->vol, 0, vol_bytes, s)
                                  : cudaMemcpyAsync(h->vol, volume, vol_bytes, cudaMemcpyHostToDevice, s);
-    for (int c = 0; e == cudaSuccess && st == FDK_OK && c * C < n_views; ++c) {
-        const int b = c & 1, v0 = c * C;
-        const int nv = (n_views - v0 < C) ? n_views - v0 : C;
+    bool copied_back = false;
+    for (int c = 0, v0 = 0; e == cudaSuccess && st == FDK_OK && c < (int)sizes.size(); v0 += sizes[c++]) {
+        const int b = c & 1, nv = sizes[c];
         if (c >= 2) e = cudaStreamWaitEvent(h->copy, h->consumed[b], 0);   // buffer b is free
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h->chunk[b], static_cast<const char *>(projections) + (size_t)v0 * plane * esz,
@@ -876,15 +925,38 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
         if (e == cudaSuccess) e = cudaEventRecord(h->copied[b], h->copy);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->copied[b], 0);
         if (e != cudaSuccess) break;
-        st = fdk_backproject(h->vol, dims, voxel_size, origin, h->chunk[b], det, matrices + (size_t)v0 * 12, nv,
-                             &oc);
-        if (st == FDK_OK) e = cudaEventRecord(h->consumed[b], s);
+        const float *mk = matrices + (size_t)v0 * 12;
+        // AUTO resolved once per chunk on the whole volume, so that slabs take the same path
+        oc.fetch = o->fetch;
+        if (oc.fetch == FDK_FETCH_AUTO)
+            oc.fetch = auto_takes_stage(g, h->chunk[b], mk, nv, &oc) ? FDK_FETCH_STAGE : FDK_FETCH_LDG;
+        if (c + 1 < (int)sizes.size() || !slabs) {
+            st = fdk_backproject(h->vol, dims, voxel_size, origin, h->chunk[b], det, mk, nv, &oc);
+        } else {
+            for (int z0 = 0, k = 0; st == FDK_OK && e == cudaSuccess && z0 < g.nz; z0 += slab_z, ++k) {
+                const int nz = (g.nz - z0 < slab_z) ? g.nz - z0 : slab_z;
+                const int32_t sd[3] = {g.nx, g.ny, nz};
+                const float so[3] = {origin[0], origin[1],
+                                     (float)((double)origin[2] + (double)z0 * (double)voxel_size[2])};
+                st = fdk_backproject(h->vol + (size_t)z0 * slice, sd, voxel_size, so, h->chunk[b], det, mk, nv,
+                                     &oc);
+                if (st == FDK_OK) e = cudaEventRecord(h->slab_done[k], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->slab_done[k], 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(volume + (size_t)z0 * slice, h->vol + (size_t)z0 * slice,
+                                        (size_t)nz * slice * sizeof(float), cudaMemcpyDeviceToHost, h->copy);
+            }
+            copied_back = true;
+        }
+        if (st == FDK_OK && e == cudaSuccess) e = cudaEventRecord(h->consumed[b], s);
     }
-    if (e == cudaSuccess && st == FDK_OK) e = cudaMemcpyAsync(volume, h->vol, vol_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && st == FDK_OK && !copied_back)
+        e = cudaMemcpyAsync(volume, h->vol, vol_bytes, cudaMemcpyDeviceToHost, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
-    cudaStreamSynchronize(h->copy);
+    cudaError_t e3 = cudaStreamSynchronize(h->copy);
     if (st) return st;
     if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = e3;
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("host back-projection: %s", cudaGetErrorString(e));

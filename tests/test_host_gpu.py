@@ -3,8 +3,10 @@ ABI, with the projections copied in chunks of views that overlap the
 back-projection of the previous chunk.
 
 One chunk is one fdk_backproject pass, so with fewer than 64 views the
-result equals the device entry point bit for bit; with more, each chunk is
-its own pass and the result matches the FP64 oracle within the accuracy bar.
+result equals the device entry point bit for bit, also when the volume is
+tall enough (nz >= 64) for the last chunk to run as z-slabs that are copied
+back one by one.  With more views each chunk is its own pass and the result
+matches the FP64 oracle within the accuracy bar.
 """
 import os
 
@@ -39,10 +41,26 @@ def test_one_chunk_equals_device_path_bitwise():
     assert torch.equal(host, dev.cpu())
 
 
+@pytest.mark.parametrize("fetch", [fdk.FETCH_AUTO, fdk.FETCH_LDG])
+def test_one_chunk_in_z_slabs_equals_device_path_bitwise(fetch):
+    """80 slices: the single chunk runs as slabs of 32, 32 and 16 slices
+    (whole 16-voxel tile layers, exact FP32 slab origins), each copied back
+    while the next is computed; the volume equals one device call's."""
+    s = synth.make_scan(synth.preset("small", nx=40, ny=36, nz=80, voxel=4.0, n_views=40), device="cuda")
+    dev = torch.zeros(_shape(s), device="cuda")
+    fdk.fdk_backproject(dev, s["proj"], s["mats"], s["voxel_size"], s["origin"], fetch=fetch)
+    for pinned in (True, False):
+        host = torch.full(_shape(s), 3.0)
+        host = host.pin_memory() if pinned else host
+        fdk.fdk_backproject_host(host, s["proj"].cpu().pin_memory(), s["mats"], s["voxel_size"], s["origin"],
+                                 fetch=fetch, overwrite=True)
+        assert torch.equal(host, dev.cpu()), f"pinned={pinned}"
+
+
 @pytest.mark.parametrize("pinned", [True, False])
-def test_four_chunks_accumulate_against_oracle(pinned):
-    """300 views go in four chunks of 75; the host volume starts at 0.5 and
-    is accumulated twice."""
+def test_chunks_accumulate_against_oracle(pinned):
+    """300 views go in chunks of 19, 38, 76 and 167 views; the host volume
+    starts at 0.5 and is accumulated twice."""
     s = synth.make_scan(synth.preset("small", n_views=300, det_w=40, det_h=32, nx=20, ny=18, nz=10))
     ref = _oracle(s)
     vol = torch.full(_shape(s), 0.5)
