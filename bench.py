@@ -347,7 +347,8 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
         fdk.fdk_backproject_host(h_vol, h_proj, mats, vs, org, fetch=args.fetch, tile=args.tile,
                                  overwrite=True)
 
-    e2e_step()
+    for _ in range(max(args.warmup, 3)):
+        e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
