@@ -101,6 +101,21 @@ def test_adjoint_full_detector_sampled_views():
     assert_parity(ref, got, what="adjoint 256^3")
 
 
+def test_adjoint_512_cube_sampled_views():
+    """The transpose on the 512^3 workload in the launch configuration the
+    benchmark times (host matrices, one launch per ray orientation, the
+    16-voxel z-run this geometry takes): a seeded Gaussian 512^3 volume onto
+    4 of the 496 views, whole 1248 x 960 images, against the oracle."""
+    cfg = synth.PRESETS["fdk512"]
+    geo = synth.geometry(cfg)
+    pick = np.linspace(0, cfg.n_views - 1, 4).astype(int)
+    dims, vs, org = synth.volume_geometry(cfg)
+    s = {"cfg": cfg, "mats": geo["mats"][pick], "dims": dims, "voxel_size": vs, "origin": org}
+    x = synth.gaussian_volume(dims, seed=37)
+    got = _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert_parity(_oracle_adj(s, x), got, what="adjoint 512^3")
+
+
 def test_adjoint_fine_voxels_16_voxel_run():
     """0.5 mm voxels on the 1248 x 960 detector (the 512^3 workload's pitch),
     a 96 x 96 x 40 centre block, 32 views spread over the scan: the volume
