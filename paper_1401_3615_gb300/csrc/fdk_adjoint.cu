@@ -18,6 +18,10 @@
 // cell can overflow whatever the geometry, and each contribution is
 // rounded to 1/s, about 1e-6 of a typical contribution.  Footprints too
 // large for the shared buffer fall back to direct FP32 global atomics.
+//
+// Tiles are 16 x 16 voxels in x, y with a z-run of 8 or 16 voxels per thread.
+// The host picks the run per call: 16 where the volume stays far from every
+// source and the footprints fit half the buffer, else 8.
 #include "fdk_tile.cuh"
 
 namespace fdk {
