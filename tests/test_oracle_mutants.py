@@ -40,6 +40,16 @@ MUTANTS = {
                                       "const double du = (double)m - v0, dv = (double)n - u0;"),
     "focal length without the u0 term": ("const double f2 = G[0][0] / s2 - u0 * u0;",
                                          "const double f2 = G[0][0] / s2;"),
+    "v from the u row": ("double v = vp / w;", "double v = up / w;"),
+    "z step with the y voxel size": ("double Z = jb->org[2] + (double)z * jb->vs[2];",
+                                     "double Z = jb->org[2] + (double)z * jb->vs[1];"),
+    "ramp kernel centre tap 1/2": ("h[d] = (d == 0) ? 0.25 :", "h[d] = (d == 0) ? 0.5 :"),
+    "even ramp taps nonzero": ("((d % 2) ? -1.0 / (pi * pi * (double)d * (double)d) : 0.0)",
+                               "(-1.0 / (pi * pi * (double)d * (double)d))"),
+    "cosine weight squared": ("f / sqrt(f * f + du * du + dv * dv)", "f * f / (f * f + du * du + dv * dv)"),
+    "views overwrite instead of accumulate": ("row[x] += val * iw2;", "row[x] = val * iw2;"),
+    "last detector row dropped": ("n < 0 || n >= H) return 0.0;", "n < 0 || n >= H - 1) return 0.0;"),
+    "filter scale dropped": ("o[m] = scale * acc;", "o[m] = acc;"),
 }
 
 
