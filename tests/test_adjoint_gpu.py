@@ -48,6 +48,18 @@ def test_adjoint_parity_ragged(ragged):
     assert_parity(ref, got, what="adjoint")
 
 
+def test_adjoint_anisotropic_voxels_offset_origin():
+    """Voxel pitches of 9, 11 and 13 mm along x, y and z and an origin off
+    the isocentre."""
+    s = synth.make_scan(synth.preset("small", nx=37, ny=29, nz=21), device="cuda")
+    vs = np.array([9.0, 11.0, 13.0], np.float32)
+    s["voxel_size"] = vs
+    s["origin"] = (-(s["dims"].astype(np.float64) - 1) / 2.0 * vs + np.array([6.0, -4.0, 9.0])).astype(np.float32)
+    x = synth.gaussian_volume(s["dims"], seed=38)
+    assert_parity(_oracle_adj(s, x), _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy(),
+                  what="adjoint, anisotropic")
+
+
 def test_adjoint_accumulates_and_multi_pass():
     s = synth.make_scan(synth.preset("small", n_views=600, det_w=40, det_h=32, nx=20, ny=18, nz=10),
                         device="cuda")

@@ -32,7 +32,12 @@ def _small_batch(n=12, seed=77):
                            seed=int(rng.integers(1, 1 << 30)))
         s = synth.make_scan(cfg, device="cuda")
         vol = torch.zeros((nz, ny, nx), device="cuda")
-        scans.append((vol, s["proj"], s["mats"], s["voxel_size"], s["origin"]))
+        vs, org = s["voxel_size"], s["origin"]
+        if i % 3 == 1:   # anisotropic pitches and an origin off the isocentre
+            vs = (vs * np.array([0.8, 1.0, 1.25], np.float32)).astype(np.float32)
+            org = (-(np.array([nx, ny, nz], np.float64) - 1) / 2.0 * vs
+                   + rng.uniform(-5.0, 5.0, size=3)).astype(np.float32)
+        scans.append((vol, s["proj"], s["mats"], vs, org))
     return scans
 
 
