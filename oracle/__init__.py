@@ -63,9 +63,12 @@ def _load():
             lib.oracle_camera.argtypes = [_f32p, ctypes.c_int64, _f64p]
             lib.oracle_preweight_filter.argtypes = [_f64p, _f32p, ctypes.c_int64, ctypes.c_int64,
                                                     _f32p, ctypes.c_int64, ctypes.c_double]
+            lib.oracle_count_updates.argtypes = [_i64p, _i64p, _i64p, _f64p, _f64p, ctypes.c_int64,
+                                                 ctypes.c_int64, _f32p, ctypes.c_int64, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int]
             for fn in (lib.oracle_backproject, lib.oracle_backproject_voxels,
                        lib.oracle_adjoint, lib.oracle_bruteforce, lib.oracle_camera,
-                       lib.oracle_preweight_filter):
+                       lib.oracle_preweight_filter, lib.oracle_count_updates):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -188,3 +191,21 @@ def preweight_filter(proj, mats, scale: float = 1.0) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_preweight_filter failed ({rc})")
     return out
+
+
+def count_updates(mats, dims, voxel_size, origin, det_w: int, det_h: int, eps: float = 1e-3,
+                  eps_w: float = 1e-5, threads: int = 1):
+    """The clipped update count: (voxel, view) pairs with w > 0, -1 < u < W
+    and -1 < v < H (Sec. VII).  Returns (count, band), band being the pairs
+    within eps pixels (eps_w in w) of one of those decisions, which a lower
+    precision evaluation may decide either way."""
+    d, vs, org = _geom(dims, voxel_size, origin)
+    m = np.ascontiguousarray(np.asarray(mats, dtype=np.float32).reshape(-1, 12))
+    c = np.zeros(1, dtype=np.int64)
+    b = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_count_updates(_p(c, _i64p), _p(b, _i64p), _p(d, _i64p), _p(vs, _f64p), _p(org, _f64p),
+                                      int(det_w), int(det_h), _p(m, _f32p), m.shape[0], float(eps),
+                                      float(eps_w), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_count_updates failed ({rc})")
+    return int(c[0]), int(b[0])

@@ -32,7 +32,8 @@
  * Parity pins live in the tests: constant projections (closed form
  * c * sum_k 1/w_k^2), an orthographic matrix that copies the image into the
  * volume, brute-force tent sums, linearity, scale, view chunking, view
- * permutation, the adjoint dot product and the thread split.
+ * permutation, the adjoint dot product and the thread split; for the
+ * clipped update count, orthographic closed forms and a vectorised count.
  */
 #include <math.h>
 #include <pthread.h>
@@ -385,5 +386,93 @@ int oracle_preweight_filter(double *out, const float *proj, int64_t W, int64_t H
     free(cam);
     free(h);
     free(g);
+    return 0;
+}
+
+/* The clipped update count (the basis of the paper's GUp/s figures,
+ * Sec. VII): the (voxel, view) pairs with w > 0, -1 < u < W and -1 < v < H,
+ * the pairs that can touch the detector under the bilinear taps with zero
+ * outside.  Also counted, in *band, are the pairs that sit within eps of one
+ * of those decisions (|w| <= eps_w, or u or v within eps pixels of -1, W or
+ * H while w > 0): an evaluation in lower precision may decide those either
+ * way, and no other pair.  Threads split (z, y) lines; the counts are exact
+ * integers, so the split does not change them. */
+typedef struct {
+    const float *mats;
+    int64_t nx, ny, W, H, n_views;
+    double vs[3], org[3], eps, eps_w;
+    int64_t line_begin, line_end;
+    int64_t count, band;
+} count_job;
+
+static void *count_worker(void *arg)
+{
+    count_job *jb = (count_job *)arg;
+    int64_t count = 0, band = 0;
+    const double Wd = (double)jb->W, Hd = (double)jb->H, e = jb->eps;
+    for (int64_t k = 0; k < jb->n_views; ++k) {
+        double P[12];
+        for (int q = 0; q < 12; ++q) P[q] = (double)jb->mats[k * 12 + q];
+        for (int64_t line = jb->line_begin; line < jb->line_end; ++line) {
+            int64_t z = line / jb->ny, y = line % jb->ny;
+            double Z = jb->org[2] + (double)z * jb->vs[2];
+            double Y = jb->org[1] + (double)y * jb->vs[1];
+            for (int64_t x = 0; x < jb->nx; ++x) {
+                double X = jb->org[0] + (double)x * jb->vs[0];
+                double w = P[8] * X + P[9] * Y + P[10] * Z + P[11];
+                if (fabs(w) <= jb->eps_w) { ++band; continue; }
+                if (!(w > 0.0)) continue;
+                double u = (P[0] * X + P[1] * Y + P[2] * Z + P[3]) / w;
+                double v = (P[4] * X + P[5] * Y + P[6] * Z + P[7]) / w;
+                if (u > -1.0 && u < Wd && v > -1.0 && v < Hd) ++count;
+                if (fabs(u + 1.0) <= e || fabs(u - Wd) <= e || fabs(v + 1.0) <= e || fabs(v - Hd) <= e) ++band;
+            }
+        }
+    }
+    jb->count = count;
+    jb->band = band;
+    return NULL;
+}
+
+int oracle_count_updates(int64_t *count, int64_t *band, const int64_t dims[3], const double voxel_size[3],
+                         const double origin[3], int64_t W, int64_t H, const float *mats, int64_t n_views,
+                         double eps, double eps_w, int nthreads)
+{
+    if (!count || !band || check_geom(dims, W, H, n_views)) return -1;
+    *count = 0;
+    *band = 0;
+    int64_t lines = dims[1] * dims[2];
+    if (lines == 0 || dims[0] == 0 || n_views == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > ORACLE_MAX_THREADS) nthreads = ORACLE_MAX_THREADS;
+    if (nthreads > lines) nthreads = (int)lines;
+    count_job *jobs = (count_job *)calloc((size_t)nthreads, sizeof(count_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    for (int t = 0; t < nthreads; ++t) {
+        count_job *jb = &jobs[t];
+        jb->mats = mats;
+        jb->nx = dims[0]; jb->ny = dims[1];
+        jb->W = W; jb->H = H; jb->n_views = n_views;
+        for (int q = 0; q < 3; ++q) { jb->vs[q] = voxel_size[q]; jb->org[q] = origin[q]; }
+        jb->eps = eps;
+        jb->eps_w = eps_w;
+        jb->line_begin = lines * t / nthreads;
+        jb->line_end = lines * (t + 1) / nthreads;
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, count_worker, &jobs[t]) != 0) break;
+        started = t;
+    }
+    count_worker(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    for (int t = started + 1; t < nthreads; ++t) count_worker(&jobs[t]);
+    for (int t = 0; t < nthreads; ++t) {
+        *count += jobs[t].count;
+        *band += jobs[t].band;
+    }
+    free(jobs);
+    free(th);
     return 0;
 }

@@ -72,6 +72,20 @@ def test_adjoint_accumulates_and_multi_pass():
     assert_parity(ref, proj.cpu().numpy())
 
 
+def test_adjoint_device_matrices_multi_pass():
+    """Matrices in device memory, which the host cannot read to group the
+    views by ray orientation: one launch per pass in view order, here 600
+    views in two passes."""
+    s = synth.make_scan(synth.preset("small", n_views=600, det_w=40, det_h=32, nx=20, ny=18, nz=10),
+                        device="cuda")
+    x = synth.gaussian_volume(s["dims"], seed=39)
+    proj = torch.zeros((600, 32, 40), device="cuda")
+    fdk.fdk_forwardproject_adjoint(proj, torch.from_numpy(x).cuda(), torch.from_numpy(s["mats"]).cuda(),
+                                   s["voxel_size"], s["origin"])
+    torch.cuda.synchronize()
+    assert_parity(_oracle_adj(s, x), proj.cpu().numpy(), what="adjoint, device matrices")
+
+
 def test_adjoint_source_inside_volume():
     """The source circle (radius 150 mm) lies within the 400 mm x-y extent
     of the volume, so tiles straddle the source's principal plane and hold

@@ -228,6 +228,28 @@ def test_sampled_512_cube_496_views():
     print(f"fdk512 sampled ({len(xyz)} voxels): max|diff|/peak = {err / peak:.3e}")
 
 
+@pytest.mark.parametrize("case", ["fdk128", "source inside", "fdk512, 16 views"])
+def test_count_updates_against_oracle(case):
+    """The clipped update count (the units of the benchmark's roofline) against
+    the oracle's FP64 count: the device decides in FP32, so the two may
+    differ only on the pairs the oracle finds within 1e-3 px (1e-5 in w) of
+    a decision, and never by more than their number."""
+    if case == "fdk128":
+        cfg = synth.PRESETS["fdk128"]
+    elif case == "source inside":
+        cfg = synth.preset("small", nx=40, ny=40, nz=8, voxel=10.0, sid=150.0, sdd=300.0)
+    else:
+        cfg = synth.PRESETS["fdk512"]
+    mats = synth.geometry(cfg)["mats"]
+    if case.startswith("fdk512"):
+        mats = mats[np.linspace(0, cfg.n_views - 1, 16).astype(int)]
+    dims, vs, org = synth.volume_geometry(cfg)
+    got = fdk.fdk_count_updates(dims, (cfg.det_w, cfg.det_h), mats, vs, org)
+    ref, band = oracle.count_updates(mats, dims, vs, org, cfg.det_w, cfg.det_h, threads=NCPU)
+    assert ref > 0
+    assert abs(got - ref) <= band, (case, got, ref, band)
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_precision_form_1024_subblock(dtype):
     """The storage-precision workload: 1024^3 FP32 volume, 496 views of

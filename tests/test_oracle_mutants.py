@@ -50,6 +50,9 @@ MUTANTS = {
     "views overwrite instead of accumulate": ("row[x] += val * iw2;", "row[x] = val * iw2;"),
     "last detector row dropped": ("n < 0 || n >= H) return 0.0;", "n < 0 || n >= H - 1) return 0.0;"),
     "filter scale dropped": ("o[m] = scale * acc;", "o[m] = acc;"),
+    "count keeps pairs behind the source": ("if (!(w > 0.0)) continue;", "if (w == 0.0) continue;"),
+    "count on [0, W) x [0, H)": ("if (u > -1.0 && u < Wd && v > -1.0 && v < Hd) ++count;",
+                                 "if (u >= 0.0 && u < Wd && v >= 0.0 && v < Hd) ++count;"),
 }
 
 

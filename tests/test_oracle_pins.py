@@ -336,3 +336,57 @@ def test_filter_matches_fft_route_of_generator():
     # the generator scales by d_beta * tau and its kernel carries 1/tau^2
     q = oracle.preweight_filter(raw.float().numpy(), geo["mats"], scale=dbeta / tau)
     np.testing.assert_allclose(q, filt, rtol=0, atol=2e-6 * np.abs(filt).max())
+
+
+def test_count_orthographic_closed_form():
+    """w = 1, u = x/s + o_x/s, v = y/s + o_y/s: the pairs with -1 < u < W and
+    -1 < v < H are counted in closed form.  Half-voxel offsets keep every
+    pair 0.5 px from a decision (empty band); integer offsets put the column
+    u = W exactly on one, where the strict bound excludes it and the band
+    holds it."""
+    P = np.stack([_ortho(2.0), _ortho(2.0)]).reshape(2, 12)
+    dims, W, H = (10, 5, 3), 6, 8
+    # u = x - 0.5: x in 0..6 (7 columns); v = y - 0.5: y in 0..4 (all 5 rows)
+    c, b = oracle.count_updates(P, dims, (2, 2, 2), (-1.0, -1.0, 0.0), W, H)
+    assert (c, b) == (2 * 7 * 5 * 3, 0)
+    # u = x: x in 0..5 counted, x = 6 (u = W) in the band only
+    c, b = oracle.count_updates(P, dims, (2, 2, 2), (0.0, 0.0, 0.0), W, H)
+    assert (c, b) == (2 * 6 * 5 * 3, 2 * 1 * 5 * 3)
+
+
+def test_count_matches_numpy_brute_force():
+    """The threaded C count against a vectorised numpy evaluation of the same
+    definition, on the tiny scan and on a volume that holds the source
+    circle (w <= 0 pairs), for count and band alike, with any thread split."""
+    for s in (_scan("tiny"), _scan("small", nx=40, ny=40, nz=8, voxel=10.0, sid=150.0, sdd=300.0)):
+        d, vs, org = s["dims"], s["voxel_size"].astype(np.float64), s["origin"].astype(np.float64)
+        W, H = s["cfg"].det_w, s["cfg"].det_h
+        zz, yy, xx = np.meshgrid(*(np.arange(int(d[a])) for a in (2, 1, 0)), indexing="ij")
+        X = np.stack([org[0] + xx * vs[0], org[1] + yy * vs[1], org[2] + zz * vs[2],
+                      np.ones(xx.shape)], -1).reshape(-1, 4)
+        cnt = band = 0
+        for P in s["mats"].astype(np.float64):
+            q = X @ P.T
+            w = q[:, 2]
+            near_w = np.abs(w) <= 1e-5
+            front = (w > 0) & ~near_w
+            u = np.where(front, q[:, 0] / np.where(front, w, 1.0), 0.0)
+            v = np.where(front, q[:, 1] / np.where(front, w, 1.0), 0.0)
+            cnt += int(np.sum(front & (u > -1) & (u < W) & (v > -1) & (v < H)))
+            edge = (np.abs(u + 1) <= 1e-3) | (np.abs(u - W) <= 1e-3) | (np.abs(v + 1) <= 1e-3) | (np.abs(v - H) <= 1e-3)
+            band += int(np.sum(near_w)) + int(np.sum(front & edge))
+        for threads in (1, 3):
+            assert oracle.count_updates(s["mats"], d, s["voxel_size"], s["origin"], W, H,
+                                        threads=threads) == (cnt, band)
+
+
+def test_count_scale_and_behind_source():
+    """P -> 2P leaves u and v and the sign of w, so the count; P -> -P puts
+    every voxel behind the source, so nothing is counted."""
+    s = _scan("small")
+    args = (s["dims"], s["voxel_size"], s["origin"], s["cfg"].det_w, s["cfg"].det_h)
+    c, _ = oracle.count_updates(s["mats"], *args)
+    assert c > 0
+    assert oracle.count_updates((2.0 * s["mats"]).astype(np.float32), *args)[0] == c
+    assert oracle.count_updates((-s["mats"]).astype(np.float32), *args)[0] == 0
+
