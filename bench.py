@@ -168,6 +168,12 @@ def _cpu_sample(cfg, scan_proj, mats, dims, vs, org, target_s: float, threads: i
     return upd / dt, desc, dt
 
 
+def _workload(args, cfg) -> str:
+    """The workload's name, the same on both arms."""
+    return (f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} FP32 volume ({cfg.voxel} mm), {cfg.n_views} views of "
+            f"{cfg.det_w}x{cfg.det_h} {args.proj_dtype.upper()} filtered projections, 200-degree short scan")
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -206,8 +212,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} volume, {cfg.n_views} views "
-                               f"of {cfg.det_w}x{cfg.det_h}", "sample": "bounded slab per step"},
+        "config": {"workload": _workload(args, cfg), "updates_per_step": cfg.updates,
+                   "sample": "bounded slab per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"central slab {nx}x{ny}x{planes}, all {cfg.n_views} views per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -505,9 +511,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": (f"{args.config}: {cfg.nx}x{cfg.ny}x{cfg.nz} FP32 volume "
-                                    f"({cfg.voxel} mm), {cfg.n_views} views of {cfg.det_w}x{cfg.det_h} "
-                                    f"{args.proj_dtype.upper()} filtered projections, 200-degree short scan"),
+            "config": {"workload": _workload(args, cfg),
                        "updates_per_step": upd_full, "clipped_updates_per_step": upd_clip,
                        "l2": (f"inputs larger than L2 (projections {proj.numel() * proj.element_size() / 1e9:.2f} GB, "
                               f"volume {vol.numel() * 4 / 2**20:.0f} MiB)"),
