@@ -28,7 +28,8 @@
  * that are allocated on first use for a detector shape, cached per device and
  * reused by later calls (fdk_release() frees them); calls that share one
  * cache entry are ordered by an event, whatever their streams.  The LDG path
- * allocates nothing.  Calls enqueue kernels on opts->stream and return;
+ * allocates nothing; the STAGE path allocates only a 4-byte error word per
+ * device on first use.  Calls enqueue kernels on opts->stream and return;
  * asynchronous faults surface at the caller's next synchronisation.
  *
  * Errors: argument problems return FDK_ERR_INVALID_ARG before anything is
