@@ -137,7 +137,6 @@ fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
     static_assert(32 % WX == 0 && BX % WX == 0 && BY % (32 / WX) == 0, "warp tiling");
     static_assert(R % 2 == 0, "z-run must be even (voxel pairs)");
     constexpr int KCHUNK = kStageChunk;
-    constexpr unsigned NWARPS = BX * BY / 32;
     __shared__ ViewEntry tab[KCHUNK];
     __shared__ int4 sbox[KCHUNK];
     __shared__ unsigned char cls[KCHUNK];
