@@ -154,7 +154,7 @@ struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
     Timer() { cudaEventCreate(&a); cudaEventCreate(&b); }
     ~Timer() { cudaEventDestroy(a); cudaEventDestroy(b); }
-    double ms(cudaStream_t s)
+    double ms()
     {
         cudaEventSynchronize(b);
         float v = 0.0f;
@@ -172,7 +172,7 @@ double sm_mhz(cudaStream_t s, unsigned long long *dcyc)
     cudaEventRecord(t.a, s);
     micro_clock_kernel<<<1, 1, 0, s>>>(dcyc, spin);
     cudaEventRecord(t.b, s);
-    const double ms = t.ms(s);
+    const double ms = t.ms();
     unsigned long long cyc = 0;
     cudaMemcpy(&cyc, dcyc, sizeof cyc, cudaMemcpyDeviceToHost);
     return ms > 0.0 ? (double)cyc / (ms * 1e3) : 0.0;
@@ -234,7 +234,7 @@ fdk_status fdk_microbench(int32_t which, int32_t param, double *result)
         cudaEventRecord(t.a, s);
         launch();
         cudaEventRecord(t.b, s);
-        const double ms = t.ms(s);
+        const double ms = t.ms();
         const double mhz = sm_mhz(s, dcyc);
         return (ms > 0.0 && mhz > 0.0) ? warp_ops / ((double)sms * ms * 1e-3 * mhz * 1e6) : 0.0;
     };
