@@ -428,8 +428,7 @@ def run_ours(args):
     # per-launch durations (a step's launches run back to back), CUDA events on the launching stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    clocks = ClockSampler(local, args.clocks_csv)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
@@ -646,6 +645,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also write the raw nvidia-smi samples of the timed region to this file")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
