@@ -261,6 +261,7 @@ static fdk_status quad_stage_get(int dev, int W, int H, int dtype, int n, QuadSt
         }
         cudaError_t e = cudaMalloc(&t->buf, need);
         if (e != cudaSuccess) {
+            t->buf = nullptr;
             cudaGetLastError();
             set_error("quad staging: cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? FDK_ERR_OOM : FDK_ERR_CUDA;
@@ -454,10 +455,14 @@ static fdk_status err_word(int dev, unsigned **out)
     for (auto &p : g_errw)
         if (p.first == dev) { *out = p.second; return FDK_OK; }
     unsigned *w = nullptr;
-    if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess || cudaMemset(w, 0, sizeof(unsigned)) != cudaSuccess) {
+    if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
-        if (w) cudaFree(w);
         return fail(FDK_ERR_OOM, "error-word allocation failed");
+    }
+    if (cudaMemset(w, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(w);
+        return fail(FDK_ERR_CUDA, "error-word initialisation failed");
     }
     g_errw.push_back({dev, w});
     *out = w;
@@ -797,27 +802,31 @@ static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, 
         g_host.emplace_back(new HostStage());
         h = g_host.back().get();
         h->dev = dev;
-        if (cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(FDK_ERR_CUDA, "copy stream creation failed");
-        }
-        for (int b = 0; b < 2; ++b)
-            if (cudaEventCreateWithFlags(&h->copied[b], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->consumed[b], cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(FDK_ERR_CUDA, "event creation failed");
-            }
-        for (cudaEvent_t &ev : h->slab_done)
-            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(FDK_ERR_CUDA, "event creation failed");
-            }
     }
+    // created on first use, and again by a later call if a creation failed
+    if (!h->copy && cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        h->copy = nullptr;
+        cudaGetLastError();
+        return fail(FDK_ERR_CUDA, "copy stream creation failed");
+    }
+    std::vector<cudaEvent_t *> events;
+    for (int b = 0; b < 2; ++b) {
+        events.push_back(&h->copied[b]);
+        events.push_back(&h->consumed[b]);
+    }
+    for (cudaEvent_t &ev : h->slab_done) events.push_back(&ev);
+    for (cudaEvent_t *ev : events)
+        if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+            *ev = nullptr;
+            cudaGetLastError();
+            return fail(FDK_ERR_CUDA, "event creation failed");
+        }
     if (h->vol_bytes < vol_bytes) {
         cudaFree(h->vol);
         h->vol = nullptr;
         h->vol_bytes = 0;
         if (cudaMalloc(&h->vol, vol_bytes) != cudaSuccess) {
+            h->vol = nullptr;
             cudaGetLastError();
             return fail(FDK_ERR_OOM, "device volume allocation failed");
         }
@@ -831,6 +840,7 @@ static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, 
         h->chunk_bytes = 0;
         for (int b = 0; b < 2; ++b)
             if (cudaMalloc(&h->chunk[b], chunk_bytes) != cudaSuccess) {
+                h->chunk[b] = nullptr;
                 cudaGetLastError();
                 return fail(FDK_ERR_OOM, "device projection chunk allocation failed");
             }
@@ -1050,7 +1060,11 @@ fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float 
     cudaStream_t s = (cudaStream_t)o->stream;
     unsigned long long *dcount = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&dcount, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) { set_error("cudaMallocAsync: %s", cudaGetErrorString(e)); return FDK_ERR_OOM; }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("count buffer: cudaMallocAsync failed: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FDK_ERR_OOM : FDK_ERR_CUDA;
+    }
     cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s);
     static thread_local BpArgs a;
     for (int v0 = 0; v0 < n_views && st == FDK_OK; v0 += KMAX) {
