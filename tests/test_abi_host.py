@@ -150,3 +150,36 @@ def test_staged_fetch_checks_before_cuda():
             setattr(o, field, val)
         st = _call_bp(opts=o, **kw)
         assert st != fdk.FDK_OK and msg in fdk.fdk_last_error(), (field, fdk.fdk_last_error())
+
+
+def test_host_memory_is_refused_no_cpu_fallback():
+    """The device entry points never compute on the host: CPU tensors are
+    refused by the library's pointer check (here, without a GPU, the check
+    itself cannot succeed), and the call raises instead of falling back."""
+    import numpy as np
+    import torch
+    vol = torch.zeros((4, 4, 4), dtype=torch.float32)
+    proj = torch.ones((1, 8, 8), dtype=torch.float32)
+    mats = np.eye(3, 4, dtype=np.float32).reshape(1, 12)
+    with pytest.raises(fdk.FdkError) as e:
+        fdk.fdk_backproject(vol, proj, mats, (1, 1, 1), (0, 0, 0), stream=0)
+    assert e.value.status == fdk.FDK_ERR_INVALID_ARG and "volume" in str(e.value)
+    with pytest.raises(fdk.FdkError) as e:
+        fdk.fdk_forwardproject_adjoint(proj, vol, mats, (1, 1, 1), (0, 0, 0), stream=0)
+    assert e.value.status == fdk.FDK_ERR_INVALID_ARG
+    assert float(vol.abs().sum()) == 0.0 and float(proj.sum()) == 64.0   # nothing written
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """With no library and no way to build one, the first call raises; the
+    binding has nothing to fall back on."""
+    monkeypatch.setattr(fdk, "_lib", None)
+    monkeypatch.setattr(fdk_build, "OUT", str(tmp_path / "_build"))
+    monkeypatch.setattr(fdk_build, "LIB", str(tmp_path / "_build" / "libfdk.so"))
+
+    def no_nvcc():
+        raise RuntimeError("nvcc not found")
+    monkeypatch.setattr(fdk_build, "nvcc", no_nvcc)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        fdk.fdk_version()
+    assert fdk._lib is None
