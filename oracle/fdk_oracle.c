@@ -43,10 +43,12 @@
 
 #define ORACLE_MAX_THREADS 1024
 
-/* One voxel against one view: detector cell (i, j), weights (a, b) and
- * 1/w^2.  Returns 0 when the voxel contributes nothing: w <= 0 (behind the
- * source), or all four taps outside the W x H image (then every tap reads
- * zero, so skipping is exact and keeps the int64 conversion defined). */
+/* One voxel against one view (Sec. IV, Listing 1: the projection, the
+ * dehomogenisation and the cell of the bilinear taps): detector cell
+ * (i, j), weights (a, b) and 1/w^2.  Returns 0 when the voxel contributes
+ * nothing: w <= 0 (behind the source), or all four taps outside the W x H
+ * image (then every tap reads zero, so skipping is exact and keeps the int64
+ * conversion defined). */
 static int oracle_cell(const double P[12], double X, double Y, double Z, int64_t W, int64_t H,
                        int literal_trunc, int64_t *i, int64_t *j, double *a, double *b,
                        double *inv_w2)
@@ -123,7 +125,8 @@ static int check_geom(const int64_t dims[3], int64_t W, int64_t H, int64_t n_vie
     return 0;
 }
 
-/* Back-project n_views projections into vol (nz, ny, nx) doubles, +=.
+/* Back-project n_views projections into vol (nz, ny, nx) doubles, +=
+ * (Sec. IV, Listing 1, applied once per projection).
  * The thread split is over collapsed (z, y) lines in equal static chunks,
  * as the paper's OpenMP collapse(z, y) schedule (Sec. VI); every voxel still
  * sums its views in index order, so any nthreads gives the same bits. */
@@ -164,7 +167,8 @@ int oracle_backproject(double *vol, const int64_t dims[3], const double voxel_si
     return 0;
 }
 
-/* Back-project into a list of voxels only: out[q] += f at voxel
+/* Back-project into a list of voxels only (Sec. IV, Listing 1, restricted
+ * to the listed voxels): out[q] += f at voxel
  * (xyz[3q], xyz[3q+1], xyz[3q+2]).  Same arithmetic as oracle_backproject,
  * used to check sampled voxels of volumes too large for the full oracle. */
 int oracle_backproject_voxels(double *out, const int64_t *xyz, int64_t n_vox,
@@ -238,7 +242,9 @@ static void *adj_worker(void *arg)
     return NULL;
 }
 
-/* Transpose of oracle_backproject: proj_out (n_views, H, W) doubles +=
+/* Transpose of oracle_backproject, the operator of Sec. IV, Listing 1 (the
+ * paper has no adjoint; this is the plain transpose of that definition):
+ * proj_out (n_views, H, W) doubles +=
  * sum over voxels of vol * (tap weight) / w^2.  Threads split views, so each
  * detector pixel is written by one thread in (z, y, x) voxel order. */
 int oracle_adjoint(double *proj_out, const int64_t dims[3], const double voxel_size[3],
@@ -275,7 +281,9 @@ int oracle_adjoint(double *proj_out, const int64_t dims[3], const double voxel_s
     return 0;
 }
 
-/* Brute force for tiny cases: f(X) = sum_k sum_{m,n} I_k[n,m] tent(u-m)
+/* Brute force for tiny cases of Sec. IV, Listing 1, whose bilinear
+ * interpolation with zero outside the detector is, written as a sum over
+ * every pixel, f(X) = sum_k sum_{m,n} I_k[n,m] tent(u-m)
  * tent(v-n) / w^2 with tent(t) = max(0, 1-|t|), evaluated over every pixel.
  * No floor, no cell, no bounds branches: a different route to the same
  * bilinear, zero-extended interpolation. */
