@@ -311,21 +311,27 @@ FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *s
  */
 FDK_API fdk_status fdk_batch_plan_execute(fdk_batch_plan plan, void *stream);
 
-/* The tile variant a plan uses (the autotuner's pick when it ran). */
+/* The tile variant a plan uses (the autotuner's pick when it ran).  A service
+ * call of the batched form; the paper has no counterpart. */
 FDK_API fdk_status fdk_batch_plan_tile(fdk_batch_plan plan, int32_t *tile);
 
-/* Free a plan's device memory.  No execution of it may still be in flight. */
+/* Free a plan's device memory.  No execution of it may still be in flight.
+ * A service call; the paper has no counterpart. */
 FDK_API void fdk_batch_plan_destroy(fdk_batch_plan plan);
 
-/* Create, execute on opts->stream, synchronise that stream, destroy. */
+/* The batched form in one call (each scan as fdk_backproject, Listing 1,
+ * Sec. IV): create, execute on opts->stream, synchronise that stream,
+ * destroy. */
 FDK_API fdk_status fdk_backproject_batched(const fdk_scan *scans, int32_t n_scans,
                                            const fdk_opts *opts);
 
-/* Synchronise the current device, then report whether a bounded device-side
- * wait of an earlier call on it gave up (FDK_ERR_TIMEOUT; the tiles whose
- * wait gave up were left unwritten) or the device reported an error
- * (FDK_ERR_CUDA).  Clears the timeout record.  Only the FDK_FETCH_STAGE path
- * has such waits. */
+/* A service call (the paper has no counterpart).  Synchronise the current
+ * device, then report whether a bounded device-side wait of an earlier call
+ * on it gave up (FDK_ERR_TIMEOUT) or the device reported an error
+ * (FDK_ERR_CUDA).  Clears the timeout record.  Two paths have such waits:
+ * the FDK_FETCH_STAGE back-projection (a tile whose wait gave up is left
+ * unwritten) and fdk_preweight_filter's staged rows (a CTA whose wait gave
+ * up leaves its remaining row pairs unwritten). */
 FDK_API fdk_status fdk_device_status(void);
 
 /* Gather micro-benchmarks of the device (the GB300 counterpart of the
@@ -352,7 +358,8 @@ typedef enum fdk_micro {
 } fdk_micro;
 FDK_API fdk_status fdk_microbench(int32_t which, int32_t param, double *result);
 
-/* Message for the last non-OK status returned on this thread ("" if none). */
+/* Message for the last non-OK status returned on this thread ("" if none).
+ * The service calls below have no counterpart in the paper. */
 FDK_API const char *fdk_last_error(void);
 
 /* Drop cached per-buffer state (texture arrays, staging buffers, spectra,

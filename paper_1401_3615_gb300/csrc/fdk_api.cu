@@ -596,8 +596,8 @@ fdk_status fdk_device_status(void)
     }
     if (h) {
         cudaMemset(w, 0, sizeof(unsigned));
-        return fail(FDK_ERR_TIMEOUT, "a bounded wait of the staged back-projection gave up; "
-                                     "the tiles concerned were not written");
+        return fail(FDK_ERR_TIMEOUT, "a bounded device-side wait gave up (staged back-projection or "
+                                     "row filter); the tiles or rows concerned were not written");
     }
     return FDK_OK;
 }
