@@ -78,3 +78,29 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
                           "ref_step_seconds": 1.0})()
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle on a bounded slab of the
+    named workload and prints one JSON line with the bench contract's keys
+    (here on the small test scan, so it runs in a second on the CPU)."""
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    args = type("A", (), {"config": "small", "steps": 2, "warmup": 1, "gpus": 1,
+                          "ref_step_seconds": 0.05, "proj_dtype": "f32"})()
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GUp/s"
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 1)
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["dtype"] == "f64" and line["data"] == "synthetic"
+    assert line["config"]["workload"].startswith("small: 24x20x18")
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["value"] == line["value"] and cpu["cores"] >= 1
+    assert "slab" in cpu["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GUp/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
