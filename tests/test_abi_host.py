@@ -183,3 +183,95 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     with pytest.raises(RuntimeError, match="nvcc not found"):
         fdk.fdk_version()
     assert fdk._lib is None
+
+
+def _geom_args(dims=(4, 4, 4), det=(8, 8)):
+    return ((ctypes.c_int32 * 3)(*dims), (ctypes.c_float * 3)(1, 1, 1), (ctypes.c_float * 3)(0, 0, 0),
+            (ctypes.c_int32 * 2)(*det), (ctypes.c_float * 12)(*([1.0] * 12)))
+
+
+def test_adjoint_and_count_validate_before_cuda():
+    lib = _raw()
+    d, vs, org, det, m = _geom_args()
+    o = fdk.fdk_opts()
+    o.proj_dtype = fdk.FDK_BF16
+    st = lib.fdk_forwardproject_adjoint(ctypes.c_void_p(256), det, ctypes.c_void_p(256), d, vs, org, m, 1,
+                                        ctypes.byref(o))
+    assert st == fdk.FDK_ERR_INVALID_ARG and "FP32" in fdk.fdk_last_error()
+    st = lib.fdk_forwardproject_adjoint(ctypes.c_void_p(256), det, None, d, vs, org, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "volume" in fdk.fdk_last_error()
+    bad = (ctypes.c_int32 * 3)(4, 4, 0)
+    st = lib.fdk_forwardproject_adjoint(ctypes.c_void_p(256), det, ctypes.c_void_p(256), bad, vs, org, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "dims" in fdk.fdk_last_error()
+    assert lib.fdk_forwardproject_adjoint(None, det, ctypes.c_void_p(256), d, vs, org, m, 0, None) == fdk.FDK_OK
+    st = lib.fdk_count_updates(None, d, vs, org, det, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "count" in fdk.fdk_last_error()
+    cnt = ctypes.c_int64(-1)
+    assert lib.fdk_count_updates(ctypes.byref(cnt), d, vs, org, det, m, 0, None) == fdk.FDK_OK
+    assert cnt.value == 0
+
+
+def test_filter_validates_before_cuda():
+    lib = _raw()
+    m = (ctypes.c_float * 12)(*([1.0] * 12))
+    p = ctypes.c_void_p(256)
+    for det, n, scale, mats, msg in [((5000, 8), 1, 1.0, m, "4096"), ((0, 8), 1, 1.0, m, "det"),
+                                     ((64, 8), -1, 1.0, m, "n_views"),
+                                     ((64, 8), 1, float("inf"), m, "scale"),
+                                     ((64, 8), 1, 1.0, None, "null"),
+                                     ((64, 8), 1, 1.0, (ctypes.c_float * 12)(*([1.0] * 8 + [0.0] * 4)),
+                                      "not a camera")]:
+        st = lib.fdk_preweight_filter(p, p, (ctypes.c_int32 * 2)(*det), mats, n, scale, None)
+        assert st == fdk.FDK_ERR_INVALID_ARG and msg in fdk.fdk_last_error(), (det, n, scale, fdk.fdk_last_error())
+    assert lib.fdk_preweight_filter(p, p, (ctypes.c_int32 * 2)(64, 8), m, 0, 1.0, None) == fdk.FDK_OK
+
+
+def test_batch_plan_validates_before_cuda():
+    lib = _raw()
+    plan = ctypes.c_void_p(0)
+    sc = fdk.fdk_scan()
+    sc.volume, sc.projections = 256, 256
+    sc.dims[:] = (4, 4, 4)
+    sc.voxel_size[:] = (1, 1, 1)
+    sc.det[:] = (8, 8)
+    mats = (ctypes.c_float * 12)(*([1.0] * 12))
+    sc.matrices = ctypes.cast(mats, ctypes.c_void_p).value
+    sc.n_views = 1
+    assert lib.fdk_batch_plan_create(None, ctypes.byref(sc), 1, None) == fdk.FDK_ERR_INVALID_ARG
+    for field, val, msg in [("proj_dtype", fdk.FDK_F16, "FP32"), ("fetch", fdk.FETCH_STAGE, "LDG"),
+                            ("matrices_on_device", 1, "host matrices"), ("tile", 6, "tile"),
+                            ("autotune", 2, "autotune")]:
+        o = fdk.fdk_opts()
+        setattr(o, field, val)
+        st = lib.fdk_batch_plan_create(ctypes.byref(plan), ctypes.byref(sc), 1, ctypes.byref(o))
+        assert st == fdk.FDK_ERR_INVALID_ARG and msg in fdk.fdk_last_error(), (field, fdk.fdk_last_error())
+        assert not plan.value
+    assert lib.fdk_batch_plan_create(ctypes.byref(plan), ctypes.byref(sc), 0, None) == fdk.FDK_ERR_INVALID_ARG
+    sc.dims[1] = 0
+    st = lib.fdk_batch_plan_create(ctypes.byref(plan), ctypes.byref(sc), 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "scan 0: dims" in fdk.fdk_last_error()
+    sc.dims[1] = 4
+    sc.volume = None
+    st = lib.fdk_batch_plan_create(ctypes.byref(plan), ctypes.byref(sc), 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "null buffer" in fdk.fdk_last_error()
+    assert lib.fdk_backproject_batched(ctypes.byref(sc), 0, None) == fdk.FDK_ERR_INVALID_ARG
+
+
+def test_static_entry_point_validates_before_cuda():
+    """The allocation-free variant refuses other fetch paths and detectors
+    whose quad image exceeds its fixed array, before any CUDA call."""
+    lib = _raw()
+    d, vs, org, det, m = _geom_args()
+    o = fdk.fdk_opts()
+    o.fetch = fdk.FETCH_LDG
+    st = lib.fdk_backproject_static(ctypes.c_void_p(256), d, vs, org, ctypes.c_void_p(256), det, m, 1,
+                                    ctypes.byref(o))
+    assert st == fdk.FDK_ERR_INVALID_ARG and "FDK_FETCH_QUAD" in fdk.fdk_last_error()
+    big = (ctypes.c_int32 * 2)(2600, 2600)          # (W+3)(H+3) * 16 B = 108 MB > 64 MiB
+    st = lib.fdk_backproject_static(ctypes.c_void_p(256), d, vs, org, ctypes.c_void_p(256), big, m, 1, None)
+    assert st == fdk.FDK_ERR_INVALID_ARG and "static staging array" in fdk.fdk_last_error()
+    o = fdk.fdk_opts()
+    o.proj_dtype = fdk.FDK_F16                     # 8 B cells: 54 MB fits
+    st = lib.fdk_backproject_static(ctypes.c_void_p(256), d, vs, org, ctypes.c_void_p(256), big, m, 0,
+                                    ctypes.byref(o))
+    assert st == fdk.FDK_OK
