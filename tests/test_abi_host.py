@@ -275,3 +275,22 @@ def test_static_entry_point_validates_before_cuda():
     st = lib.fdk_backproject_static(ctypes.c_void_p(256), d, vs, org, ctypes.c_void_p(256), big, m, 0,
                                     ctypes.byref(o))
     assert st == fdk.FDK_OK
+
+
+def test_host_entry_point_retries_failed_setup():
+    """Without a GPU, the host-buffer path gets through its argument checks
+    and fails creating its copy stream.  A second call must try that set-up
+    again and fail the same way, rather than run on with the null handles
+    the first call left in its cache."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a CUDA device")
+    lib = _raw()
+    vol = np.zeros((4, 4, 4), np.float32)
+    proj = np.ones((1, 8, 8), np.float32)
+    d, vs, org, det, m = _geom_args()
+    for _ in range(2):
+        st = lib.fdk_backproject_host(vol.ctypes.data, d, vs, org, proj.ctypes.data, det, m, 1, None)
+        assert st == fdk.FDK_ERR_CUDA and "copy stream creation failed" in fdk.fdk_last_error()
+    assert not vol.any()
