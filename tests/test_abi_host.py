@@ -294,3 +294,18 @@ def test_host_entry_point_retries_failed_setup():
         st = lib.fdk_backproject_host(vol.ctypes.data, d, vs, org, proj.ctypes.data, det, m, 1, None)
         assert st == fdk.FDK_ERR_CUDA and "copy stream creation failed" in fdk.fdk_last_error()
     assert not vol.any()
+
+
+def test_count_reports_a_failed_buffer_allocation():
+    """Without a GPU the clipped count gets through its argument checks and
+    its device buffer cannot be allocated: the failure is a CUDA error (not
+    out of memory), named in the message, and *count stays 0."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a CUDA device")
+    lib = _raw()
+    d, vs, org, det, m = _geom_args()
+    cnt = ctypes.c_int64(-1)
+    st = lib.fdk_count_updates(ctypes.byref(cnt), d, vs, org, det, m, 1, None)
+    assert st == fdk.FDK_ERR_CUDA and "count buffer" in fdk.fdk_last_error()
+    assert cnt.value == 0
