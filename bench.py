@@ -119,6 +119,55 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _accuracy(args, scan, proj, mats, vs, org, dims):
+    """One back-projection of the step's workload into a zeroed volume, every
+    voxel against the FP64 oracle run on all host cores: max|diff| over
+    max|f_oracle| and PSNR (peak max|f_oracle|), the accuracy bar being
+    max|diff| <= 1e-4 max|f| and PSNR >= 80 dB."""
+    import torch
+    import oracle
+    from paper_1401_3615_gb300 import fdk
+    oracle.build()
+    threads = os.cpu_count() or 1
+    vol = torch.zeros((int(dims[2]), int(dims[1]), int(dims[0])), dtype=torch.float32, device=proj.device)
+    fdk.fdk_backproject(vol, proj, mats, vs, org, fetch=args.fetch, tile=args.tile)
+    got = vol.cpu().numpy()
+    del vol
+    t = time.perf_counter()
+    ref = oracle.backproject(proj.float().cpu().numpy(), mats, dims, vs, org, threads=threads)
+    dt = time.perf_counter() - t
+    peak = float(np.abs(ref).max())
+    diff = got.astype(np.float64) - ref
+    err = float(np.abs(diff).max())
+    mse = float(np.mean(diff * diff))
+    return {"max_abs_diff_over_peak": err / peak,
+            "psnr_db": float(10 * np.log10(peak * peak / mse)) if mse > 0 else float("inf"),
+            "voxels": int(ref.size), "against": "FP64 oracle, whole volume, same inputs",
+            "bar": "max|diff| <= 1e-4 max|f_oracle| and PSNR >= 80 dB",
+            "meets_bar": bool(err <= 1e-4 * peak and (mse == 0 or 10 * np.log10(peak * peak / mse) >= 80.0)),
+            "oracle_seconds": dt, "oracle_threads": threads}
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,7 +263,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": _workload(args, cfg), "updates_per_step": cfg.updates,
                    "sample": "bounded slab per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu_model": _cpu_model(),
+                         "kind": "oracle",
                          "sample": f"central slab {nx}x{ny}x{planes}, all {cfg.n_views} views per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -497,6 +547,9 @@ def run_ours(args):
             "algorithmic_bytes_per_step": alg_bytes,
             "binding": "issue",
         }
+        accuracy = None
+        if not args.no_accuracy and proj32 is None:
+            accuracy = _accuracy(args, scan, proj, mats, vs, org, dims)
         cpu = None
         if world == 1 and not args.no_cpu:
             import oracle
@@ -504,8 +557,8 @@ def run_ours(args):
             threads = os.cpu_count() or 1
             rate, desc, _ = _cpu_sample(cfg, proj.float().cpu().numpy(), mats, dims, vs, org,
                                         args.cpu_seconds, threads)
-            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-                   "sample": desc}
+            cpu = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "cpu_model": _cpu_model(),
+                   "kind": "oracle", "sample": desc}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -516,6 +569,20 @@ def run_ours(args):
                               f"volume {vol.numel() * 4 / 2**20:.0f} MiB)"),
                        "fetch": args.fetch, "tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "value_is": ("the forward back-projection (fdk_backproject): voxel updates nx*ny*nz*N per step "
+                         "over the step time (the full count); the adjoint is reported under 'adjoint' and "
+                         "both under 'figures' in both update counts"),
+            "figures": {
+                "forward": {"ms_per_step": ms_step, "gups_full_count": value,
+                            "gups_clipped": _job_rate(world, upd_clip, ms_step * 1e-3)},
+                "adjoint": None if adjoint is None else {
+                    "ms_per_step": adjoint["ms_per_step"], "gups_full_count": adjoint["value"],
+                    "gups_clipped": _job_rate(world, upd_clip, adjoint["ms_per_step"] * 1e-3),
+                    "ratio_to_forward": adjoint["ratio_to_forward"]},
+                "update_counts": {"full": upd_full, "clipped": upd_clip,
+                                  "clipped_is": "voxel/view pairs with w > 0, -1 < u < W, -1 < v < H "
+                                                "(the paper's GUp/s basis)"}},
+            "accuracy": accuracy,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -651,6 +718,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-preprocess", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the whole-volume comparison with the oracle (about 40 s of host time)")
     ap.add_argument("--batched", action="store_true", help="time the batched form instead")
     ap.add_argument("--micro", action="store_true", help="run the gather micro-benchmarks instead")
     ap.add_argument("--batch-scans", type=int, default=32)

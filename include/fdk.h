@@ -22,8 +22,10 @@
  *  - the library ACCUMULATES (volume +=, as the listing is called once per
  *    projection); the caller zeroes the volume first if needed.
  *
- * Memory: every buffer is owned by the caller.  "device" means a pointer the
- * current CUDA device can dereference (cudaMalloc, torch CUDA tensors).  The
+ * Memory: every buffer is owned by the caller.  "device" means memory of the
+ * CURRENT CUDA device (cudaMalloc, torch CUDA tensors); kernels run on the
+ * current device, so device memory of another GPU is refused
+ * (FDK_ERR_INVALID_ARG), managed memory is accepted.  The
  * QUAD and TEX fetch paths stage the images in library-owned device buffers
  * that are allocated on first use for a detector shape, cached per device and
  * reused by later calls (fdk_release() frees them); calls that share one
@@ -225,13 +227,24 @@ FDK_API fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], co
  * image is larger than the array is rejected with FDK_ERR_INVALID_ARG.
  *
  * Arguments, layouts and results are those of fdk_backproject; opts->fetch
- * must be FDK_FETCH_AUTO or FDK_FETCH_QUAD.  The first call on a device
- * looks up the array's device address with that device current; make that
- * first call before any stream capture.  All calls on a device share the
- * array, and each call writes every cell it reads before reading it, so
- * nothing carries over from an earlier call; calls whose work overlaps on
- * the GPU (other streams, other host threads) race on the array and give
- * undefined results.
+ * must be FDK_FETCH_AUTO or FDK_FETCH_QUAD.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream capture.
+ * When the array takes device memory: CUDA loads the library's device code
+ * per device lazily by default (CUDA_MODULE_LOADING=LAZY), and that lookup
+ * is what loads the array's module, so the 64 MiB are taken at the first
+ * call on a device, not when the library is loaded.  A caller that reserves
+ * the device's memory for its own pool makes one call before reserving it:
+ * a call with n_views = 0 (projections and matrices may then be NULL) does
+ * the set-up and nothing else.  With CUDA_MODULE_LOADING=EAGER the array is
+ * taken when the library's code is loaded.  After cudaDeviceReset, call
+ * fdk_release() first: the looked-up address belongs to the old context.
+ *
+ * All calls on a device share the array, and each call writes every cell it
+ * reads before reading it, so nothing carries over from an earlier call;
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on the array and give undefined results.
  */
 FDK_API fdk_status fdk_backproject_static(float *volume, const int32_t dims[3],
                                           const float voxel_size[3], const float origin[3],
@@ -363,8 +376,9 @@ FDK_API fdk_status fdk_microbench(int32_t which, int32_t param, double *result);
 FDK_API const char *fdk_last_error(void);
 
 /* Drop cached per-buffer state (texture arrays, staging buffers, spectra,
- * host-path buffers) on all devices.  Call only when no work that uses them
- * is in flight. */
+ * host-path buffers, error words, the static array's looked-up addresses) on
+ * all devices.  Call only when no work that uses them is in flight, and
+ * after a cudaDeviceReset before the next call. */
 FDK_API void fdk_release(void);
 
 /* ABI version, currently 1. */

@@ -6,6 +6,7 @@
 
 #include <math.h>
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -29,6 +30,50 @@ static fdk_status fail(fdk_status st, const char *msg)
     set_error("%s", msg);
     return st;
 }
+
+// Testing hooks (include/fdk_testing.h): allocations still to fail, and the
+// poll limit of the consumer waits.
+static std::atomic<int> g_fail_allocs{0};
+static std::atomic<long long> g_wait_limit{kWaitLimit};
+
+// True when this allocation is to fail (and counts it).
+static bool injected_alloc_failure()
+{
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
+cudaError_t lib_malloc(void **p, size_t bytes)
+{
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
+cudaError_t lib_malloc_array(cudaArray_t *arr, const cudaChannelFormatDesc *ch, size_t w, size_t h,
+                             unsigned flags)
+{
+    if (injected_alloc_failure()) {
+        *arr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocArray(arr, ch, w, h, flags);
+}
+
+long long consumer_wait_limit() { return g_wait_limit.load(); }
 
 static const fdk_opts kDefaultOpts = {FDK_F32, 0, nullptr, FDK_FETCH_AUTO, 0, 0, 0, {0}};
 
@@ -103,6 +148,18 @@ static fdk_status check_device_ptr(const void *p, const char *what)
     }
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
         set_error("%s must be device memory", what);
+        return FDK_ERR_INVALID_ARG;
+    }
+    // kernels run on the current device: memory of another GPU would be a
+    // fault there (or a silent peer read), so it is refused
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s: cudaGetDevice failed", what);
+        return FDK_ERR_CUDA;
+    }
+    if (attr.type == cudaMemoryTypeDevice && attr.device != cur) {
+        set_error("%s lives on device %d but device %d is current", what, attr.device, cur);
         return FDK_ERR_INVALID_ARG;
     }
     return FDK_OK;
@@ -183,7 +240,7 @@ static fdk_status tex_stage_get(int dev, int W, int H, int dtype, int n, TexStag
     const cudaChannelFormatDesc ch = tex_channel(dtype);
     while ((int)t->arrays.size() < n) {
         cudaArray_t arr = nullptr;
-        cudaError_t e = cudaMallocArray(&arr, &ch, W, H, cudaArrayTextureGather);
+        cudaError_t e = lib_malloc_array(&arr, &ch, W, H, cudaArrayTextureGather);
         if (e != cudaSuccess) {
             cudaGetLastError();
             set_error("texture staging: cudaMallocArray failed: %s", cudaGetErrorString(e));
@@ -259,7 +316,7 @@ static fdk_status quad_stage_get(int dev, int W, int H, int dtype, int n, QuadSt
             t->buf = nullptr;
             t->bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&t->buf, need);
+        cudaError_t e = lib_malloc(&t->buf, need);
         if (e != cudaSuccess) {
             t->buf = nullptr;
             cudaGetLastError();
@@ -455,7 +512,7 @@ static fdk_status err_word(int dev, unsigned **out)
     for (auto &p : g_errw)
         if (p.first == dev) { *out = p.second; return FDK_OK; }
     unsigned *w = nullptr;
-    if (cudaMalloc(&w, sizeof(unsigned)) != cudaSuccess) {
+    if (lib_malloc((void **)&w, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "error-word allocation failed");
     }
@@ -502,7 +559,7 @@ static fdk_status spectrum_get(int dev, int N, const float **out, const float2 *
             return FDK_OK;
         }
     float *p = nullptr;
-    if (cudaMalloc(&p, sizeof(float) * N + sizeof(float2) * N) != cudaSuccess) {
+    if (lib_malloc((void **)&p, sizeof(float) * N + sizeof(float2) * N) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "filter spectrum allocation failed");
     }
@@ -562,6 +619,7 @@ const char *fdk_last_error(void) { return g_err; }
 int32_t fdk_version(void) { return 1; }
 
 static void release_host_stages();
+namespace fdk { static void release_static_ptrs(); }
 
 void fdk_release(void)
 {
@@ -570,6 +628,22 @@ void fdk_release(void)
     release_spectra();
     release_err_words();
     release_host_stages();
+    release_static_ptrs();
+}
+
+fdk_status fdk_testing_set_wait_limit(int64_t polls)
+{
+    g_err[0] = 0;
+    g_wait_limit.store(polls < 0 ? kWaitLimit : (long long)polls);
+    return FDK_OK;
+}
+
+fdk_status fdk_testing_fail_allocations(int32_t n)
+{
+    g_err[0] = 0;
+    if (n < 0) return fail(FDK_ERR_INVALID_ARG, "n must be >= 0");
+    g_fail_allocs.store(n);
+    return FDK_OK;
 }
 
 fdk_status fdk_device_status(void)
@@ -653,6 +727,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     const int n_pass = n_views < KMAX ? n_views : KMAX;
     bool use_stage = false;
     a.err = nullptr;
+    a.wait_limit = consumer_wait_limit();
     if (want == FDK_FETCH_STAGE) {
         if (!tmap_encoder()) return fail(FDK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
         if ((st = err_word(dev, &a.err))) return st;
@@ -825,7 +900,7 @@ static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, 
         cudaFree(h->vol);
         h->vol = nullptr;
         h->vol_bytes = 0;
-        if (cudaMalloc(&h->vol, vol_bytes) != cudaSuccess) {
+        if (lib_malloc((void **)&h->vol, vol_bytes) != cudaSuccess) {
             h->vol = nullptr;
             cudaGetLastError();
             return fail(FDK_ERR_OOM, "device volume allocation failed");
@@ -839,7 +914,7 @@ static fdk_status host_stage_get(int dev, size_t vol_bytes, size_t chunk_bytes, 
         }
         h->chunk_bytes = 0;
         for (int b = 0; b < 2; ++b)
-            if (cudaMalloc(&h->chunk[b], chunk_bytes) != cudaSuccess) {
+            if (lib_malloc(&h->chunk[b], chunk_bytes) != cudaSuccess) {
                 h->chunk[b] = nullptr;
                 cudaGetLastError();
                 return fail(FDK_ERR_OOM, "device projection chunk allocation failed");
@@ -1059,7 +1134,7 @@ fdk_status fdk_count_updates(int64_t *count, const int32_t dims[3], const float 
     if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
     cudaStream_t s = (cudaStream_t)o->stream;
     unsigned long long *dcount = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&dcount, sizeof(unsigned long long), s);
+    cudaError_t e = lib_malloc_async((void **)&dcount, sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("count buffer: cudaMallocAsync failed: %s", cudaGetErrorString(e));
@@ -1104,9 +1179,20 @@ static __device__ __align__(256) unsigned char g_static_quads[FDK_STATIC_QUAD_BY
 static std::mutex g_static_mu;
 static void *g_static_ptr[256] = {};
 
+// Forget the looked-up addresses (fdk_release): after a device reset the
+// array lives at a new address in the new context.
+static void release_static_ptrs()
+{
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    for (void *&p : g_static_ptr) p = nullptr;
+}
+
 // Device address of g_static_quads on the current device, looked up once per
-// device with that device current.  (In host code the symbol is only a
-// host-side stand-in; kernels must get this address, never the symbol.)
+// device (per context: again after fdk_release) with that device current.
+// (In host code the symbol is only a host-side stand-in; kernels must get
+// this address, never the symbol.)  Under CUDA's lazy module loading this
+// lookup is what loads this file's module on the device, and with it
+// allocates the array.
 static fdk_status static_quads_ptr(void **out)
 {
     int dev = 0;
@@ -1161,13 +1247,13 @@ extern "C" fdk_status fdk_backproject_static(float *volume, const int32_t dims[3
                   qbytes, (unsigned)FDK_STATIC_QUAD_BYTES);
         return FDK_ERR_INVALID_ARG;
     }
-    if (n_views == 0) return FDK_OK;
+    void *scratch = nullptr;
+    if (n_views == 0) return static_quads_ptr(&scratch);   // set-up only
     if ((st = check_alignment(projections, dtype_size(o->proj_dtype), "projections"))) return st;
     if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
     if ((st = check_device_ptr(volume, "volume"))) return st;
     if ((st = check_device_ptr(projections, "projections"))) return st;
     if (o->matrices_on_device && (st = check_device_ptr(matrices, "matrices"))) return st;
-    void *scratch = nullptr;
     if ((st = static_quads_ptr(&scratch))) return st;
 
     static thread_local BpArgs a;
@@ -1273,7 +1359,7 @@ static fdk_status plan_autotune(fdk_batch_plan_t *p)
         vmax = std::max(vmax, (size_t)g.nx * g.ny * g.nz * sizeof(float));
     }
     float *scratch = nullptr;
-    if (cudaMalloc(&scratch, vmax) != cudaSuccess) {
+    if (lib_malloc((void **)&scratch, vmax) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "autotune: scratch volume allocation failed");
     }
@@ -1358,7 +1444,7 @@ fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, in
     const size_t off_mats = (off_ctr + sizeof(int) + 15) & ~(size_t)15;
     const size_t off_vidx = off_mats + sizeof(float) * 12 * total_views;
     const size_t bytes = off_vidx + sizeof(int) * total_views + 16;
-    if (cudaMalloc(&p->buf, bytes) != cudaSuccess) {
+    if (lib_malloc(&p->buf, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "batch plan: device allocation failed");
     }

@@ -27,17 +27,17 @@ namespace fdk {
 
 constexpr int kStages = 2;
 constexpr int kStageChunk = 64;          // views per table chunk on this path
-constexpr long long kWaitLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Bounded wait for the phase with the given parity of the mbarrier at bar.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait for the phase with the given parity of the mbarrier at bar:
+// at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -209,15 +209,17 @@ fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
             if (c == kStaged) {
                 const unsigned slot = base + kst;
                 const unsigned st = slot % kStages;
-                const bool ok = mbar_wait(full0 + 8u * st, (slot / kStages) & 1u);
+                const bool ok = mbar_wait(full0 + 8u * st, (slot / kStages) & 1u, a.wait_limit);
                 const ViewEntry e = tab[lv];
                 view_staged<R>(acc, e, dxf, dyf, stages + (size_t)st * kStageFloats);
                 ++kst;
                 if (!__syncthreads_and(ok)) {
                     if (tid == 0) {
                         atomicOr(a.err, 1u);
+                        // drain with the full limit: no copy may still be
+                        // writing this CTA's shared memory when it exits
                         for (int s = 0; s < kStages; ++s)
-                            if (nissue[s] > 0) mbar_wait(full0 + 8u * s, (nissue[s] - 1) & 1u);
+                            if (nissue[s] > 0) mbar_wait(full0 + 8u * s, (nissue[s] - 1) & 1u, kWaitLimit);
                     }
                     return;
                 }

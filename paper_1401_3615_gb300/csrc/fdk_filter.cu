@@ -55,6 +55,7 @@ struct FilterArgs {
     const float *spec;      // N spectrum values (1/N folded in)
     const float2 *tw;       // N twiddles exp(-2 pi i t / N) (the N = 4096 kernel)
     unsigned *err;          // device word set when a bounded wait gives up (staged rows)
+    long long wait_limit;   // polls before the wait for a staged row pair gives up
     float scale;
     const float *mats_dev;  // device matrices, or nullptr
     int W, H, n_views, N;
@@ -281,14 +282,13 @@ __device__ __forceinline__ void pass_in(float2 (&x)[16], const float2 *buf, cons
     dft16<INV>(x);
 }
 
-constexpr long long kFilterWaitLimit = 1LL << 22;
-
 __device__ __forceinline__ uint32_t fsmem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Bounded wait for the phase with the given parity of the mbarrier at bar.
-__device__ __forceinline__ bool fmbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait for the phase with the given parity of the mbarrier at bar:
+// at most `limit` polls.
+__device__ __forceinline__ bool fmbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
-    for (long long it = 0; it < kFilterWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -378,7 +378,7 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
         if (STAGED) {
             row1 = stages + st * kF16N;
             row2 = row1 + kF16N / 2;
-            ok = fmbar_wait(full0 + 8u * st, (unsigned)(it >> 1) & 1u);
+            ok = fmbar_wait(full0 + 8u * st, (unsigned)(it >> 1) & 1u, a.wait_limit);
         } else {
             row1 = a.in + ((long long)k * a.H + r1) * a.W;
             row2 = a.in + ((long long)k * a.H + r2) * a.W;
@@ -409,8 +409,10 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
             if (!__syncthreads_and(ok)) {
                 if (j == 0) {
                     atomicOr(a.err, 1u);
+                    // drain with the full limit: no copy may still be
+                    // writing this CTA's shared memory when it exits
                     for (int q = 0; q < 2; ++q)
-                        if (nis[q] > 0) fmbar_wait(full0 + 8u * q, (nis[q] - 1) & 1u);
+                        if (nis[q] > 0) fmbar_wait(full0 + 8u * q, (nis[q] - 1) & 1u, kWaitLimit);
                 }
                 return;
             }
@@ -496,6 +498,7 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
     a.spec = spec;
     a.tw = tw;
     a.err = err;
+    a.wait_limit = consumer_wait_limit();
     a.scale = scale;
     a.mats_dev = mats_dev;
     a.W = W;

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "fdk.h"
+#include "fdk_testing.h"
 
 namespace fdk {
 
@@ -15,6 +16,10 @@ namespace fdk {
 // travel in the kernel parameter block, so no device memory is needed for
 // them and concurrent calls on different streams cannot race.
 constexpr int KMAX = 512;
+
+// Polls of an mbarrier before a device-side wait gives up (a healthy copy
+// completes within a few polls).
+constexpr long long kWaitLimit = 1LL << 22;
 
 // Staged fetch path: per (tile, view), the pixel box holding every tap of
 // the tile is copied into shared memory by TMA as a stack of 8-row boxes of
@@ -46,6 +51,7 @@ struct BpArgs {
     int n_views;               // views in this launch (<= KMAX)
     int warp_x;                // voxels along x per warp patch: 8 (8x4) or 4 (4x8)
     unsigned *err;             // device word set when a bounded wait gives up (staged path)
+    long long wait_limit;      // polls before a consumer's wait for a staged view gives up
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
     union {
         unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
@@ -96,6 +102,17 @@ enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3, kS
 
 // Thread-local error message setter (fdk_api.cu).
 void set_error(const char *fmt, ...);
+
+// The library's device allocations, all through these wrappers (fdk_api.cu),
+// so that the testing hook fdk_testing_fail_allocations can make the next
+// ones fail as an out-of-memory device would.
+cudaError_t lib_malloc(void **p, size_t bytes);
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+cudaError_t lib_malloc_array(cudaArray_t *arr, const cudaChannelFormatDesc *ch, size_t w, size_t h,
+                             unsigned flags);
+// Poll limit for the consumer waits of the next launches: kWaitLimit unless a
+// test lowered it with fdk_testing_set_wait_limit.
+long long consumer_wait_limit();
 
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile,
                               cudaStream_t stream);

@@ -216,7 +216,7 @@ fdk_status fdk_microbench(int32_t which, int32_t param, double *result)
         return FDK_ERR_CUDA;
     }
     void *scratch = nullptr;
-    if (cudaMalloc(&scratch, bytes + 256) != cudaSuccess) {
+    if (lib_malloc(&scratch, bytes + 256) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(s);
         set_error("micro-benchmark scratch allocation failed");
@@ -251,7 +251,7 @@ fdk_status fdk_microbench(int32_t which, int32_t param, double *result)
     case FDK_MICRO_TLD4: {
         cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
         cudaArray_t arr = nullptr;
-        if (cudaMallocArray(&arr, &ch, param, param, cudaArrayTextureGather) != cudaSuccess) {
+        if (lib_malloc_array(&arr, &ch, param, param, cudaArrayTextureGather) != cudaSuccess) {
             cudaGetLastError();
             st = FDK_ERR_OOM;
             set_error("texture array allocation failed");

@@ -6,6 +6,7 @@ computes: every step of the back-projection runs in the library's kernels.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -97,6 +98,10 @@ def _load():
             lib.fdk_device_status.restype = ctypes.c_int
             lib.fdk_microbench.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
             lib.fdk_microbench.restype = ctypes.c_int
+            lib.fdk_testing_set_wait_limit.argtypes = [ctypes.c_int64]
+            lib.fdk_testing_set_wait_limit.restype = ctypes.c_int
+            lib.fdk_testing_fail_allocations.argtypes = [ctypes.c_int32]
+            lib.fdk_testing_fail_allocations.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -134,6 +139,36 @@ def fdk_microbench(which: int, param: int = 0) -> float:
 def _check(st: int):
     if st != FDK_OK:
         raise FdkError(st, fdk_last_error())
+
+
+def fdk_testing_set_wait_limit(polls: int) -> None:
+    """Testing hook (include/fdk_testing.h): poll limit of the consumer
+    waits of later launches (0: give up at once; < 0: the built-in limit)."""
+    _check(_load().fdk_testing_set_wait_limit(int(polls)))
+
+
+def fdk_testing_fail_allocations(n: int) -> None:
+    """Testing hook (include/fdk_testing.h): the library's next n device
+    allocations fail as on a device out of memory."""
+    _check(_load().fdk_testing_fail_allocations(int(n)))
+
+
+def _device_of(*tensors):
+    """The one CUDA device that every CUDA tensor among ``tensors`` lives on
+    (None if none is a CUDA tensor: the library then refuses the call).  The
+    library launches on the current device, so each call runs with this
+    device current, and tensors on different devices are refused here,
+    before any call."""
+    devs = {t.device for t in tensors if getattr(t, "is_cuda", False)}
+    if len(devs) > 1:
+        raise ValueError(f"tensors on different devices: {sorted(str(d) for d in devs)}")
+    return devs.pop() if devs else None
+
+
+def _on(*tensors):
+    """Context that makes the tensors' CUDA device current for one call."""
+    dev = _device_of(*tensors)
+    return torch.cuda.device(dev) if dev is not None else contextlib.nullcontext()
 
 
 def _ptr(t) -> int:
@@ -189,11 +224,12 @@ def fdk_backproject(volume: torch.Tensor, projections: torch.Tensor, matrices, v
     m, mptr, mdev = _mats(matrices, n)
     nz, ny, nx = volume.shape
     vs, org = _geom(voxel_size, origin)
-    o = _opts(_DTYPES[projections.dtype], mdev, stream, fetch, tile)
     lib = _load()
-    st = lib.fdk_backproject(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
-                             _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
-                             ctypes.byref(o))
+    with _on(volume, projections, m):
+        o = _opts(_DTYPES[projections.dtype], mdev, stream, fetch, tile)
+        st = lib.fdk_backproject(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
+                                 _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
+                                 ctypes.byref(o))
     _check(st)
     return volume
 
@@ -246,8 +282,10 @@ def fdk_backproject_static(volume: torch.Tensor, projections: torch.Tensor, matr
     m, mptr, mdev = _mats(matrices, n)
     nz, ny, nx = volume.shape
     vs, org = _geom(voxel_size, origin)
-    o = _opts(_DTYPES[projections.dtype], mdev, stream, FETCH_AUTO, tile)
-    st = _load().fdk_backproject_static(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
+    lib = _load()
+    with _on(volume, projections, m):
+        o = _opts(_DTYPES[projections.dtype], mdev, stream, FETCH_AUTO, tile)
+        st = lib.fdk_backproject_static(_ptr(volume), _i32_3(nx, ny, nz), vs, org, _ptr(projections),
                                         _i32_2(projections.shape[2], projections.shape[1]), mptr, n,
                                         ctypes.byref(o))
     _check(st)
@@ -266,8 +304,10 @@ def fdk_forwardproject_adjoint(projections: torch.Tensor, volume: torch.Tensor, 
     m, mptr, mdev = _mats(matrices, n)
     nz, ny, nx = volume.shape
     vs, org = _geom(voxel_size, origin)
-    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
-    st = _load().fdk_forwardproject_adjoint(_ptr(projections),
+    lib = _load()
+    with _on(projections, volume, m):
+        o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+        st = lib.fdk_forwardproject_adjoint(_ptr(projections),
                                             _i32_2(projections.shape[2], projections.shape[1]),
                                             _ptr(volume), _i32_3(nx, ny, nz), vs, org, mptr, n,
                                             ctypes.byref(o))
@@ -281,10 +321,13 @@ def fdk_count_updates(dims, det, matrices, voxel_size, origin, *, stream=None) -
         else int(matrices.reshape(-1, 12).shape[0])
     m, mptr, mdev = _mats(matrices, n)
     vs, org = _geom(voxel_size, origin)
-    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+    with _on(m):
+        o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
     out = ctypes.c_int64(0)
     d = [int(x) for x in dims]
-    st = _load().fdk_count_updates(ctypes.byref(out), _i32_3(*d), vs, org,
+    lib = _load()
+    with _on(m):
+        st = lib.fdk_count_updates(ctypes.byref(out), _i32_3(*d), vs, org,
                                    _i32_2(int(det[0]), int(det[1])), mptr, n, ctypes.byref(o))
     _check(st)
     return int(out.value)
@@ -327,7 +370,9 @@ class BatchPlan:
         o.autotune = 1 if autotune else 0
         h = ctypes.c_void_p()
         lib = _load()
-        _check(lib.fdk_batch_plan_create(ctypes.byref(h), arr, len(scans), ctypes.byref(o)))
+        self._tensors = [t for sc in scans for t in (sc[0], sc[1])]
+        with _on(*self._tensors):
+            _check(lib.fdk_batch_plan_create(ctypes.byref(h), arr, len(scans), ctypes.byref(o)))
         self._h = h
         self._lib = lib
         self.scans = list(scans)
@@ -339,8 +384,9 @@ class BatchPlan:
         return int(t.value)
 
     def execute(self, stream=None):
-        s = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
-        _check(self._lib.fdk_batch_plan_execute(self._h, ctypes.c_void_p(s)))
+        with _on(*self._tensors):
+            s = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
+            _check(self._lib.fdk_batch_plan_execute(self._h, ctypes.c_void_p(s)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -363,8 +409,11 @@ def fdk_backproject_batched(scans, *, tile: int = 0, stream=None):
     arr, keep = _scan_array(scans)
     o = fdk_opts()
     o.tile = tile
-    o.stream = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
-    _check(_load().fdk_backproject_batched(arr, len(scans), ctypes.byref(o)))
+    lib = _load()
+    with _on(*[t for sc in scans for t in (sc[0], sc[1])]):
+        o.stream = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream
+        st = lib.fdk_backproject_batched(arr, len(scans), ctypes.byref(o))
+    _check(st)
 
 
 def fdk_preweight_filter(out: torch.Tensor, raw: torch.Tensor, matrices, scale: float = 1.0,
@@ -378,8 +427,10 @@ def fdk_preweight_filter(out: torch.Tensor, raw: torch.Tensor, matrices, scale: 
         raise ValueError("out and raw must have the same shape")
     n = raw.shape[0]
     m, mptr, mdev = _mats(matrices, n)
-    o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
-    st = _load().fdk_preweight_filter(_ptr(out), _ptr(raw), _i32_2(raw.shape[2], raw.shape[1]), mptr, n,
+    lib = _load()
+    with _on(out, raw, m):
+        o = _opts(FDK_F32, mdev, stream, FETCH_AUTO, 0)
+        st = lib.fdk_preweight_filter(_ptr(out), _ptr(raw), _i32_2(raw.shape[2], raw.shape[1]), mptr, n,
                                       float(scale), ctypes.byref(o))
     _check(st)
     return out

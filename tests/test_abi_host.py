@@ -274,7 +274,12 @@ def test_static_entry_point_validates_before_cuda():
     o.proj_dtype = fdk.FDK_F16                     # 8 B cells: 54 MB fits
     st = lib.fdk_backproject_static(ctypes.c_void_p(256), d, vs, org, ctypes.c_void_p(256), big, m, 0,
                                     ctypes.byref(o))
-    assert st == fdk.FDK_OK
+    # past the size check: a zero-view call only does the set-up (the array's
+    # device address), which needs a device
+    assert st != fdk.FDK_ERR_INVALID_ARG
+    import torch
+    if not torch.cuda.is_available():
+        assert st == fdk.FDK_ERR_CUDA and "cudaGetDevice" in fdk.fdk_last_error()
 
 
 def test_host_entry_point_retries_failed_setup():
@@ -309,3 +314,41 @@ def test_count_reports_a_failed_buffer_allocation():
     st = lib.fdk_count_updates(ctypes.byref(cnt), d, vs, org, det, m, 1, None)
     assert st == fdk.FDK_ERR_CUDA and "count buffer" in fdk.fdk_last_error()
     assert cnt.value == 0
+
+
+def test_python_binding_refuses_tensors_on_two_devices():
+    """The library launches on the current device, so the binding runs each
+    call with its tensors' device current and refuses tensors that live on
+    different devices before any library call."""
+    from types import SimpleNamespace
+    import torch
+    a = SimpleNamespace(is_cuda=True, device=torch.device("cuda", 0))
+    b = SimpleNamespace(is_cuda=True, device=torch.device("cuda", 1))
+    host = SimpleNamespace(is_cuda=False, device=torch.device("cpu"))
+    with pytest.raises(ValueError, match="different devices"):
+        fdk._device_of(a, b)
+    assert fdk._device_of(a, host, None) == torch.device("cuda", 0)
+    assert fdk._device_of(host, None) is None
+
+
+def test_testing_hooks_validate_and_inject_allocation_failures():
+    """fdk_testing_fail_allocations makes the library's next allocation fail
+    as on a device out of memory: the clipped count, which allocates its
+    result word on every call, reports FDK_ERR_OOM.  The injection is used
+    up by that one call: without a GPU the next call fails for real, with a
+    CUDA error."""
+    import torch
+    lib = _raw()
+    assert lib.fdk_testing_fail_allocations(-1) == fdk.FDK_ERR_INVALID_ARG
+    assert lib.fdk_testing_set_wait_limit(0) == fdk.FDK_OK
+    assert lib.fdk_testing_set_wait_limit(-1) == fdk.FDK_OK
+    if torch.cuda.is_available():
+        pytest.skip("the second half needs a machine without a CUDA device")
+    d, vs, org, det, m = _geom_args()
+    cnt = ctypes.c_int64(-1)
+    assert lib.fdk_testing_fail_allocations(1) == fdk.FDK_OK
+    st = lib.fdk_count_updates(ctypes.byref(cnt), d, vs, org, det, m, 1, None)
+    assert st == fdk.FDK_ERR_OOM and "count buffer" in fdk.fdk_last_error()
+    st = lib.fdk_count_updates(ctypes.byref(cnt), d, vs, org, det, m, 1, None)
+    assert st == fdk.FDK_ERR_CUDA
+    assert lib.fdk_testing_fail_allocations(0) == fdk.FDK_OK

@@ -86,20 +86,21 @@ def test_adjoint_device_matrices_multi_pass():
     assert_parity(_oracle_adj(s, x), proj.cpu().numpy(), what="adjoint, device matrices")
 
 
-def test_adjoint_source_inside_volume():
+@pytest.mark.parametrize("lift_mm", [0.0, 75.0])
+def test_adjoint_source_inside_volume(lift_mm):
     """The source circle (radius 150 mm) lies within the 400 mm x-y extent
     of the volume, so tiles straddle the source's principal plane and hold
-    w <= 0 voxels, which receive nothing.  The volume sits 40 mm above the
-    plane of the source circle: a voxel that projects onto the detector is
-    then at least 83 mm deep (w >= 0.55), so no contribution hangs on a voxel
-    a few mm in front of the source, where 1/w^2 would amplify FP32 rounding
-    beyond the accuracy bar."""
+    w <= 0 voxels, which receive nothing.  Unlifted, the volume is centred
+    on the plane of the source circle and voxels sit a few mm in front of
+    the source; lifted 75 mm, a voxel that projects onto the detector is at
+    least 83 mm deep."""
     s = synth.make_scan(synth.preset("small", nx=40, ny=40, nz=8, voxel=10.0, sid=150.0, sdd=300.0),
                         device="cuda")
-    s["origin"] = s["origin"] + np.float32([0.0, 0.0, 75.0])
+    s["origin"] = s["origin"] + np.float32([0.0, 0.0, lift_mm])
     x = synth.gaussian_volume(s["dims"], seed=33)
-    assert_parity(_oracle_adj(s, x), _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy(),
-                  what="source inside")
+    rel, p = assert_parity(_oracle_adj(s, x), _gpu_adj(s, torch.from_numpy(x).cuda()).cpu().numpy(),
+                           what=f"source inside, lifted {lift_mm} mm")
+    print(f"adjoint, source inside, lifted {lift_mm} mm: max|diff|/max|f| = {rel:.3e}, PSNR = {p:.1f} dB")
 
 
 def test_adjoint_large_footprints():
@@ -234,3 +235,101 @@ def test_least_squares_reconstruction_20_steps():
             x -= g / (2.0 * lam)
     assert all(b <= a * (1 + 1e-6) for a, b in zip(losses, losses[1:])), losses
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+# The differentiation workload: 256^3 volume (1 mm voxels), 248 views of
+# 1248 x 960, the ellipsoid phantom's projections.
+
+@pytest.fixture(scope="module")
+def fdk256():
+    return synth.make_scan(synth.PRESETS["fdk256"], device="cuda")
+
+
+def _vol_shape(scan):
+    return (int(scan["dims"][2]), int(scan["dims"][1]), int(scan["dims"][0]))
+
+
+def test_dot_product_identity_256_cube_248_views(fdk256):
+    """<B y, x> = <y, B^T x> for seeded Gaussian y (248 x 960 x 1248) and x
+    (256^3), both inner products reduced in FP64."""
+    n, H, W = fdk256["proj"].shape
+    y = torch.from_numpy(synth.gaussian_projections(n, H, W, seed=401)).cuda()
+    x = torch.from_numpy(synth.gaussian_volume(fdk256["dims"], seed=402)).cuda()
+    by = torch.zeros_like(x)
+    fdk.fdk_backproject(by, y, fdk256["mats"], fdk256["voxel_size"], fdk256["origin"])
+    lhs = float((by.double() * x.double()).sum())
+    del by
+    btx = torch.zeros_like(y)
+    fdk.fdk_forwardproject_adjoint(btx, x, fdk256["mats"], fdk256["voxel_size"], fdk256["origin"])
+    rhs = float((y.double() * btx.double()).sum())
+    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    print(f"fdk256 dot product: <By,x> = {lhs:.9e}, <y,B^T x> = {rhs:.9e}, relative difference {rel:.2e}")
+    assert rel <= 1e-5, (lhs, rhs)
+
+
+def test_finite_differences_256_cube_248_views(fdk256):
+    """The gradient of L(p) = <c, B p> with respect to the projections, from
+    the autograd backward (the transpose kernel), against central
+    differences with eps = 1e-3 on 32 seeded projection pixels, at the
+    phantom's filtered projections.  B is linear, so the differences are
+    exact up to the FP32 rounding of the perturbed voxel sums (about 1e-4 of
+    the gradient here); the losses are reduced in FP64."""
+    proj = fdk256["proj"]
+    n, H, W = proj.shape
+    shape = _vol_shape(fdk256)
+    geo = (fdk256["mats"], fdk256["voxel_size"], fdk256["origin"], shape)
+    c = torch.from_numpy(synth.gaussian_volume(fdk256["dims"], seed=403)).cuda().double()
+    y = proj.clone().requires_grad_(True)
+    loss = (autograd.backproject(y, *geo).double() * c).sum()
+    loss.backward()
+    grad = y.grad.detach()
+    del y
+    rng = np.random.default_rng(404)
+    pix = np.stack([rng.integers(0, n, 32), rng.integers(0, H, 32), rng.integers(0, W, 32)], 1)
+    g = np.array([float(grad[k, j, i]) for k, j, i in pix])
+    scale = float(np.sqrt(np.mean(g ** 2)))
+    assert scale > 0
+    eps = 1e-3
+    worst = 0.0
+    for (k, j, i), gk in zip(pix, g):
+        vals = []
+        for sgn in (1.0, -1.0):
+            old = float(proj[k, j, i])
+            proj[k, j, i] = old + sgn * eps
+            vals.append(float((autograd.backproject(proj, *geo).double() * c).sum()))
+            proj[k, j, i] = old
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        err = abs(fd - gk) / max(abs(gk), scale)
+        worst = max(worst, err)
+        assert err <= 2e-3, (k, j, i, fd, gk)
+    print(f"fdk256 finite differences, 32 pixels: worst |fd - grad| / max(|grad|, rms grad) = {worst:.2e}")
+
+
+def test_least_squares_256_cube_248_views_20_steps():
+    """20 steps of gradient descent on min_x ||B^T x - y||^2 at the
+    differentiation workload's size, y the phantom's line integrals (248 x
+    960 x 1248), x a 256^3 volume, with the Lipschitz step 1 / (2 lambda_max
+    (B B^T)) from a power iteration: the loss falls at every step."""
+    cfg = synth.PRESETS["fdk256"]
+    s = synth.make_scan(cfg, device="cuda", filtered=False)
+    shape = (cfg.nz, cfg.ny, cfg.nx)
+    det = (cfg.n_views, cfg.det_h, cfg.det_w)
+    A = lambda v: autograd.forwardproject(v, s["mats"], s["voxel_size"], s["origin"], det)
+    torch.manual_seed(405)
+    v = torch.randn(shape, device="cuda")
+    for _ in range(20):
+        v = autograd.backproject(A(v), s["mats"], s["voxel_size"], s["origin"], shape)
+        v = v / v.norm()
+    lam = float((A(v).double() ** 2).sum())
+    y = s["proj"]
+    x = torch.zeros(shape, device="cuda", requires_grad=True)
+    losses = []
+    for _ in range(20):
+        loss = ((A(x) - y).double() ** 2).sum()
+        losses.append(float(loss.detach()))
+        g, = torch.autograd.grad(loss, x)
+        with torch.no_grad():
+            x -= g.float() / (2.0 * lam)
+    print("fdk256 least squares, loss / initial:", [round(l / losses[0], 4) for l in losses])
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(losses, losses[1:])), losses
+    assert losses[-1] < 0.9 * losses[0], losses
