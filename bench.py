@@ -418,10 +418,28 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     e2e_s = _max_over_ranks((time.perf_counter() - w0) / e2e_steps, world, dev)
     step_ms = [(b - a) * 1e3 for a, b in zip(marks, marks[1:])]
     vol_bytes = int(vol.numel() * vol.element_size())
+    # the same host link without the library: plain copies of the step's
+    # projections from the same pinned buffer, timed with CUDA events; stalls
+    # seen here come from the host side of the copies, not from the library
+    dst = torch.empty_like(proj)
+    st = torch.cuda.current_stream()
+    copy_ms = []
+    for _ in range(e2e_steps):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(st)
+        dst.copy_(h_proj, non_blocking=True)
+        c1.record(st)
+        torch.cuda.synchronize()
+        copy_ms.append(c0.elapsed_time(c1))
+    del dst
     return {"value": _job_rate(world, upd_full, e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
             "d2h_bytes_per_step": vol_bytes, "ms_per_step": e2e_s * 1e3,
             "ms_per_step_median": float(np.median(step_ms)), "step_ms": [round(t, 2) for t in step_ms],
+            "plain_h2d_copy_ms": {"median": float(np.median(copy_ms)), "max": float(max(copy_ms)),
+                                  "each": [round(t, 2) for t in copy_ms],
+                                  "what": "cudaMemcpyAsync of the step's projections from the same pinned "
+                                          "buffer, no library call, CUDA events"},
             "how": "fdk_backproject_host(overwrite) on pinned host buffers: projections in chunks of "
                    "views that double in size (31, 62, 124, 279 for 496) and whose copies overlap the "
                    "back-projection, the last chunk in z-slabs copied out while the next is computed; "

@@ -28,6 +28,11 @@ namespace fdk {
 
 constexpr int kAdjBX = 16, kAdjBY = 16, kAdjChunk = 64;
 constexpr int kAdjCap = 16384;  // cells of the shared footprint buffer (64 KB, dynamic)
+// Tiles whose FP32 detector positions may be off by more than this many
+// pixels (tiles close to the source) splat from FP64 positions instead.  The
+// bound stays below 1.3e-5 px on the benchmark geometries (128^3..1024^3 on
+// the 1248 x 960 detector), so they never take that path.
+constexpr float kPreciseUV = 2.0e-5f;
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
@@ -49,6 +54,14 @@ __device__ __forceinline__ void adj_tap_checked(int *acc_s, bool fixed, float sc
     }
 }
 
+// Shared-memory integer reductions into the cell at a 32-bit shared address
+// and the one after it (the offset in the instruction, not in a register).
+__device__ __forceinline__ void red_shared_pair(uint32_t addr, int v0, int v1)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(addr), "r"(v0) : "memory");
+    asm volatile("red.shared.add.s32 [%0+4], %1;" :: "r"(addr), "r"(v1) : "memory");
+}
+
 // The four weighted taps of a voxel: value g = f / w^2 and fractions (a, b).
 struct Taps {
     float w00, w10, w01, w11;
@@ -62,6 +75,51 @@ __device__ __forceinline__ Taps tap_weights(float g, float a, float b)
     t.w11 = gh * a;
     t.w01 = gh - t.w11;
     return t;
+}
+
+// Fixed-point splat of one view for an interior tile: every tap lies in
+// the image and, by the 1-pixel margin of the footprint box bb, inside bb;
+// the clamp of the cell index only guards memory.  Each f32x2 pair holds one
+// quantity of two z neighbours, as in the forward's hot loop.  The
+// contribution f / w^2 is scaled to fixed point before it is split into the
+// four tap weights, and the cell index (j - j0) * bw + (i - i0) is formed in
+// FP32 (exact: below 2^14 plus the 2^23 index magic), whose bits then address
+// the cell directly.
+template <int R>
+__device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry &e, float2 buv, float bw,
+                                            int U, int V, const int4 &bb, int npx, float scale, int *acc_v)
+{
+    const float2 BU = f2(buv.x), BV = f2(buv.y), BWW = f2(bw);
+    const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
+    const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
+    const float2 PITCH = f2((float)bb.z);
+    const float2 OFF = f2((float)((V - bb.y) * bb.z + (U - bb.x)) + kIndexMagic);
+    const float kmax = (float)(npx - bb.z - 2) + kIndexMagic;
+    const float2 SC = f2(scale);
+    const uint32_t abase = (uint32_t)__cvta_generic_to_shared(acc_v) - (kIndexBits << 2);
+    const uint32_t abase1 = abase + ((uint32_t)bb.z << 2);
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
+        const float2 wl = __ffma2_rn(RF, GW, BWW);
+        const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
+        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
+        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
+        const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
+        const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
+        const float2 g = __fmul2_rn(__fmul2_rn(iw, iw), __fmul2_rn(f2(f[r], f[r + 1]), SC));
+        const float2 gh = __fmul2_rn(g, bv), gl = __ffma2_rn(gh, NEG, g);
+        const float2 w10 = __fmul2_rn(gl, au), w00 = __ffma2_rn(w10, NEG, gl);
+        const float2 w11 = __fmul2_rn(gh, au), w01 = __ffma2_rn(w11, NEG, gh);
+        float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OFF);
+        k = f2(fminf(fmaxf(k.x, kIndexMagic), kmax), fminf(fmaxf(k.y, kIndexMagic), kmax));
+        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
+        red_shared_pair(abase + o0, __float2int_rn(w00.x), __float2int_rn(w10.x));
+        red_shared_pair(abase1 + o0, __float2int_rn(w01.x), __float2int_rn(w11.x));
+        red_shared_pair(abase + o1, __float2int_rn(w00.y), __float2int_rn(w10.y));
+        red_shared_pair(abase1 + o1, __float2int_rn(w01.y), __float2int_rn(w11.y));
+    }
 }
 
 // VEC4: rows of the projections are 16-byte aligned (W % 4 == 0 and an
@@ -156,40 +214,46 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
             const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
             const float2 gz = f2(e.b.z, e.b.w);
             const int U = (int)e.o.x, V = (int)e.o.y;
-            if (c == kInterior && fixed) {
-                // every tap is inside the image and, by the 1-pixel margin of
-                // the box, inside the footprint; the clamp only guards memory
-                // index = (j - j0) * bw + (i - i0) with i, j taken from the
-                // floor bits; the bias is folded in modulo 2^32 (unsigned)
-                const unsigned bz = (unsigned)bb.z;
-                const unsigned base = (unsigned)((V - bb.y) * bb.z + (U - bb.x)) -
-                                      ((unsigned)kFloorBits * bz + (unsigned)kFloorBits);
-                const int hi_idx = npx - bb.z - 2;
+            // FP32 rounding of the table's detector positions, about
+            // 2^-24 (|c| + extent |g|) / w pixels, bounded over the tile
+            // (uniform); the splat's tap weights move by that much.
+            const float tu = fabsf(e.a.x) + (BX / 2) * fabsf(e.a.z) + (BY / 2) * fabsf(e.b.x) +
+                             (R / 2) * fabsf(e.b.z);
+            const float tv = fabsf(e.a.y) + (BX / 2) * fabsf(e.a.w) + (BY / 2) * fabsf(e.b.y) +
+                             (R / 2) * fabsf(e.b.w);
+            const bool precise = c == kGeneral || !(wr.x > 0.0f) ||
+                                 fmaxf(tu, tv) * 5.9604645e-8f > kPreciseUV * wr.x;
+            if (precise) {
+                // close to the source (or across its plane): each voxel's
+                // (u', v', w) from the matrix in FP64 and u = u'/w, v = v'/w
+                // by division, as the definition reads
+                const int v = v0 + lv;
+                const float *Pm = a.mats_dev ? a.mats_dev + 12 * v : a.mats + 12 * v;
+                const double X = (double)a.g.org[0] + (double)x * (double)a.g.vs[0];
+                const double Y = (double)a.g.org[1] + (double)y * (double)a.g.vs[1];
+                const double bu = fma((double)Pm[0], X, fma((double)Pm[1], Y, (double)Pm[3]));
+                const double bvv = fma((double)Pm[4], X, fma((double)Pm[5], Y, (double)Pm[7]));
+                const double bww = fma((double)Pm[8], X, fma((double)Pm[9], Y, (double)Pm[11]));
+                const double pu = Pm[2], pv = Pm[6], pw = Pm[10];
 #pragma unroll
-                for (int r = 0; r < R; r += 2) {
-                    const float rf0 = (float)(r - R / 2), rf1 = rf0 + 1.0f;
-                    const float2 wl = __ffma2_rn(f2(rf0, rf1), f2(e.w.w), f2(bw));
-                    const float iw0 = rcp_approx(wl.x), iw1 = rcp_approx(wl.y);
-                    const float2 uv0 = __fmul2_rn(__ffma2_rn(f2(rf0), gz, buv), f2(iw0));
-                    const float2 uv1 = __fmul2_rn(__ffma2_rn(f2(rf1), gz, buv), f2(iw1));
-                    const float2 t0 = __fadd2_rd(uv0, f2(kFloorMagic)), t1 = __fadd2_rd(uv1, f2(kFloorMagic));
-                    const float2 ab0 = __fadd2_rn(uv0, __fadd2_rn(f2(kFloorMagic), __fmul2_rn(t0, f2(-1.0f))));
-                    const float2 ab1 = __fadd2_rn(uv1, __fadd2_rn(f2(kFloorMagic), __fmul2_rn(t1, f2(-1.0f))));
-                    const float2 g = __fmul2_rn(f2(f[r], f[r + 1]), __fmul2_rn(f2(iw0, iw1), f2(iw0, iw1)));
-                    const Taps k0 = tap_weights(g.x, ab0.x, ab0.y), k1 = tap_weights(g.y, ab1.x, ab1.y);
-                    int i0 = (int)(__float_as_uint(t0.y) * bz + __float_as_uint(t0.x) + base);
-                    int i1 = (int)(__float_as_uint(t1.y) * bz + __float_as_uint(t1.x) + base);
-                    i0 = min(max(i0, 0), hi_idx);
-                    i1 = min(max(i1, 0), hi_idx);
-                    atomicAdd(acc_v + i0, __float2int_rn(k0.w00 * scale));
-                    atomicAdd(acc_v + i0 + 1, __float2int_rn(k0.w10 * scale));
-                    atomicAdd(acc_v + i0 + bb.z, __float2int_rn(k0.w01 * scale));
-                    atomicAdd(acc_v + i0 + bb.z + 1, __float2int_rn(k0.w11 * scale));
-                    atomicAdd(acc_v + i1, __float2int_rn(k1.w00 * scale));
-                    atomicAdd(acc_v + i1 + 1, __float2int_rn(k1.w10 * scale));
-                    atomicAdd(acc_v + i1 + bb.z, __float2int_rn(k1.w01 * scale));
-                    atomicAdd(acc_v + i1 + bb.z + 1, __float2int_rn(k1.w11 * scale));
+                for (int r = 0; r < R; ++r) {
+                    if (f[r] == 0.0f) continue;
+                    const double Z = (double)a.g.org[2] + (double)(z0 + r) * (double)a.g.vs[2];
+                    const double wd = fma(pw, Z, bww);
+                    if (!(wd > 0.0)) continue;
+                    const double ud = fmin(fmax(fma(pu, Z, bu) / wd, -2.0), (double)W + 1.0);
+                    const double vd = fmin(fmax(fma(pv, Z, bvv) / wd, -2.0), (double)H + 1.0);
+                    const double fu = floor(ud), fv = floor(vd);
+                    const Taps k = tap_weights((float)((double)f[r] / (wd * wd)), (float)(ud - fu),
+                                               (float)(vd - fv));
+                    const int i = (int)fu, j = (int)fv;
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i, j, k.w00);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j, k.w10);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i, j + 1, k.w01);
+                    adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
                 }
+            } else if (fixed && c == kInterior) {
+                splat_fixed<R>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
             } else {
                 const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
                 const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
@@ -216,15 +280,20 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
             }
             if (fits) {
                 __syncthreads();
-                // cells hold fixed point (scaled ints) or FP32 bits; both are
-                // zero when untouched and are reset to zero after the flush
                 if (VEC4) {
                     const int gw = bb.z >> 2;
                     int4 *acc4 = reinterpret_cast<int4 *>(acc_v);
+                    // (row, group) of p, stepped along with p (one division per view)
+                    int row = tid / gw, grp = tid - row * gw;
+                    const int drow = NT / gw, dgrp = NT - drow * gw;
                     for (int p = tid; p < (npx >> 2); p += NT) {
                         const int4 s4 = acc4[p];
+                        const int col = grp << 2, rw = row;
+                        grp += dgrp;
+                        row += drow;
+                        if (grp >= gw) { grp -= gw; ++row; }
                         if ((s4.x | s4.y | s4.z | s4.w) != 0) {
-                            const int row = p / gw, col = (p - row * gw) << 2;
+                            const int row = rw;
                             const float4 v = fixed
                                 ? make_float4((float)s4.x * inv_scale, (float)s4.y * inv_scale,
                                               (float)s4.z * inv_scale, (float)s4.w * inv_scale)

@@ -782,6 +782,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
             if ((st = launch_make_quads(a.proj, qstage->buf, nv, g.W, g.H, o->proj_dtype, s))) return st;
             a.quads = qstage->buf;
         }
+        a.walk_y = 0;
         if (o->matrices_on_device || use_tex) {
             // one launch over the pass in view order with 8 x 4 warp patches
             a.n_views = nv;
@@ -812,6 +813,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
             if (cnt == 0) continue;
             a.n_views = cnt;
             a.warp_x = group == 0 ? 4 : 8;
+            a.walk_y = group == 1 && use_stage;
             if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
         }
     }

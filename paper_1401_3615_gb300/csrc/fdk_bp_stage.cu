@@ -12,8 +12,9 @@
 //
 // Pipeline per CTA: kStages shared-memory stages.  Every thread waits on the
 // stage's mbarrier and computes the view; after a CTA barrier (the stage is
-// then free) thread 0 issues the copy of the staged view kStages further on
-// into it, so the next view's copy is in flight while the CTA computes.
+// then free) warp 0 issues the copy of the staged view kStages further on
+// into it, one 8-row box per lane, so the next view's copy is in flight
+// while the CTA computes.
 // Each thread owns a z-run of 16 voxels, so the per-view barrier is shared
 // by 16 updates per thread (8 per thread measured 10% slower, 24 slower
 // still).  (A barrier-free variant, in which the last warp done with a stage
@@ -78,12 +79,20 @@ __device__ __forceinline__ void stage_issue(const BpArgs &a, int v0, int lv, con
     }
 }
 
-// Shared-memory load at a 32-bit shared address.  Volatile, so it stays after
-// the (volatile) mbarrier wait that makes the stage's data visible.
+// Shared-memory loads of the words at a 32-bit shared address and the one
+// after it (the offset in the instruction, not in a register).  Volatile, so
+// they stay after the (volatile) mbarrier wait that makes the stage's data
+// visible.
 __device__ __forceinline__ float lds(uint32_t addr)
 {
     float v;
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float lds_next(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+4];" : "=f"(v) : "r"(addr));
     return v;
 }
 
@@ -102,9 +111,10 @@ __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e,
     const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
     const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
     const float2 PITCH = f2(e.o.w), OZ = f2(e.o.z);
-    // 32-bit shared addresses with the index magic folded into the base
+    // 32-bit shared addresses of the tap rows j and j + 1, with the index
+    // magic folded into the bases
     const uint32_t sbase = smem_addr(stage) - (kIndexBits << 2);
-    const uint32_t bw4 = (uint32_t)(int)e.o.w << 2;
+    const uint32_t sbase1 = sbase + ((uint32_t)(int)e.o.w << 2);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
         const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
@@ -116,11 +126,10 @@ __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e,
         const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
         const float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OZ);
-        const uint32_t a0 = sbase + ((uint32_t)__float_as_int(k.x) << 2);
-        const uint32_t a1 = sbase + ((uint32_t)__float_as_int(k.y) << 2);
-        const float2 p00 = f2(lds(a0), lds(a1)), p10 = f2(lds(a0 + 4u), lds(a1 + 4u));
-        const float2 p01 = f2(lds(a0 + bw4), lds(a1 + bw4));
-        const float2 p11 = f2(lds(a0 + bw4 + 4u), lds(a1 + bw4 + 4u));
+        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
+        const uint32_t a0 = sbase + o0, a1 = sbase + o1, b0 = sbase1 + o0, b1 = sbase1 + o1;
+        const float2 p00 = f2(lds(a0), lds(a1)), p10 = f2(lds_next(a0), lds_next(a1));
+        const float2 p01 = f2(lds(b0), lds(b1)), p11 = f2(lds_next(b0), lds_next(b1));
         const float2 lo = __ffma2_rn(au, __ffma2_rn(p00, NEG, p10), p00);
         const float2 hi = __ffma2_rn(au, __ffma2_rn(p01, NEG, p11), p01);
         const float2 val = __ffma2_rn(bv, __ffma2_rn(lo, NEG, hi), lo);
@@ -154,7 +163,10 @@ fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
     const int lx = (warp % WPX) * WX + (lane % WX);
     const int ly = (warp / WPX) * WY + (lane / WX);
     const float dxf = (float)(lx - BX / 2), dyf = (float)(ly - BY / 2);
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * R;
+    // CTAs are scheduled in blockIdx.x order: walking along the rays keeps
+    // the resident CTAs' footprints overlapping, so their boxes hit in L2
+    const int tx = a.walk_y ? blockIdx.y : blockIdx.x, ty = a.walk_y ? blockIdx.x : blockIdx.y;
+    const int x0 = tx * BX, y0 = ty * BY, z0 = blockIdx.z * R;
     const int W = a.g.W, H = a.g.H;
     const float *proj = static_cast<const float *>(a.proj);
     const uint32_t full0 = smem_addr(full);
@@ -268,7 +280,8 @@ static fdk_status launch_stage_shape(const BpArgs &a, cudaStream_t s)
         set_error("staged back-projection: cudaFuncSetAttribute failed: %s", cudaGetErrorString(err));
         return FDK_ERR_CUDA;
     }
-    dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + R - 1) / R);
+    const unsigned gx = (a.g.nx + BX - 1) / BX, gy = (a.g.ny + BY - 1) / BY;
+    dim3 grid(a.walk_y ? gy : gx, a.walk_y ? gx : gy, (a.g.nz + R - 1) / R);
     k<<<grid, BX * BY, smem, s>>>(a);
     err = cudaGetLastError();
     if (err != cudaSuccess) {

@@ -50,6 +50,8 @@ struct BpArgs {
     long long plane;           // W*H elements per image
     int n_views;               // views in this launch (<= KMAX)
     int warp_x;                // voxels along x per warp patch: 8 (8x4) or 4 (4x8)
+    int walk_y;                // staged path: 1 = blockIdx.x runs along y (CTAs scheduled in
+                               // turn walk along rays that run mostly along y), 0 = along x
     unsigned *err;             // device word set when a bounded wait gives up (staged path)
     long long wait_limit;      // polls before a consumer's wait for a staged view gives up
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
