@@ -535,6 +535,14 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full)
 
+    # the training-system forms on their own workloads, beside the plain FP32 form
+    batched = None
+    if world == 1 and not args.no_batched and proj32 is None:
+        batched = {key: _batched_leg(args, cfgs, label, max(1, min(args.steps, 5)))
+                   for key, cfgs, label in _batched_workloads(args)}
+    if world == 1 and not args.no_precision and proj32 is None:
+        precision = _precision_leg(args)
+
     out = None
     if rank == 0:
         peaks = _peaks()
@@ -607,6 +615,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "preprocess": preprocess,
             "precision": precision,
+            "batched": batched,
             "gpu_launches": args.steps * passes,
             "clocks": clk,
             "clipped_gups": _job_rate(world, upd_clip, ms_step * 1e-3),
@@ -618,28 +627,25 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
-    """The batched form: 32 seeded scans of uneven size (volumes 64..384 per
-    axis, 120..496 views, detectors 640x480..1248x960, FP32), back-projected
-    (a) by 32 sequential fdk_backproject calls, (b) by one autotuned batch
-    plan, (c) by that plan replayed from a CUDA graph.  One JSON line."""
+def _batched_leg(args, cfgs, label: str, steps: int) -> dict:
+    """The batched form on one set of scans: one autotuned plan (executed,
+    and replayed from a CUDA graph) against sequential fdk_backproject calls
+    with default options; the batch's volumes are compared with the
+    sequential ones bit for bit."""
     import torch
     import synth
     from paper_1401_3615_gb300 import fdk
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    cfgs = synth.batch_scan_configs(args.batch_scans)
     scans = []
     for c in cfgs:
-        s = synth.make_scan(c, device="cuda")
-        vol = torch.zeros((c.nz, c.ny, c.nx), device="cuda")
-        scans.append((vol, s["proj"], s["mats"], s["voxel_size"], s["origin"]))
-        del s
+        sc = synth.make_scan(c, device="cuda")
+        scans.append((torch.zeros((c.nz, c.ny, c.nx), device="cuda"), sc["proj"], sc["mats"],
+                      sc["voxel_size"], sc["origin"]))
+        del sc
     updates = sum(c.updates for c in cfgs)
     stream = torch.cuda.current_stream()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed(fn, steps):
+    def timed(fn):
         for _ in range(max(args.warmup, 3)):
             fn()
         torch.cuda.synchronize()
@@ -650,45 +656,153 @@ def run_batched(args):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / steps
 
-    def sequential():
-        for vol, proj, mats, vs, org in scans:
-            fdk.fdk_backproject(vol, proj, mats, vs, org, tile=plan.tile)
-
     def sequential_default():
         for vol, proj, mats, vs, org in scans:
             fdk.fdk_backproject(vol, proj, mats, vs, org)
 
     plan = fdk.fdk_batch_plan_create(scans, autotune=True)
-    ms_seq = timed(sequential, args.steps)
-    ms_seq_default = timed(sequential_default, args.steps)
-    ms_batch = timed(plan.execute, args.steps)
+    staged = sum(plan.scan_fetch(i) == fdk.FETCH_STAGE for i in range(len(scans)))
+    ms_seq = timed(sequential_default)
+    ms_batch = timed(plan.execute)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(stream)
     with torch.cuda.graph(g, stream=s):
         plan.execute(stream=s)
-    ms_graph = timed(g.replay, args.steps)
-    line = {
-        "metric": "GUp/s, 32 uneven scans in one persistent launch (batched form)",
-        "value": updates / (ms_graph * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"{len(cfgs)} seeded scans: volumes 64..384 per axis, 120..496 views, "
-                               "detectors 640x480..1248x960, FP32",
-                   "updates_per_step": updates, "autotuned_tile": plan.tile,
-                   "views_total": sum(c.n_views for c in cfgs)},
-        "sequential_plain_calls": {"ms_per_step": ms_seq, "value": updates / (ms_seq * 1e-3) / 1e9,
-                                   "what": "fdk_backproject per scan with the plan's tile (LDG path)"},
-        "sequential_default_calls": {"ms_per_step": ms_seq_default,
-                                     "value": updates / (ms_seq_default * 1e-3) / 1e9,
-                                     "what": "fdk_backproject per scan with default options (AUTO)"},
-        "batch_plan_execute": {"ms_per_step": ms_batch, "value": updates / (ms_batch * 1e-3) / 1e9},
-        "cuda_graph_replay": {"ms_per_step": ms_graph, "value": updates / (ms_graph * 1e-3) / 1e9},
-    }
+    ms_graph = timed(g.replay)
+    # one execution from zero against the same sequential calls: bit for bit
+    equal = True
+    for i, (vol, proj, mats, vs, org) in enumerate(scans):
+        ref = torch.zeros_like(vol)
+        if plan.scan_fetch(i) == fdk.FETCH_STAGE:
+            fdk.fdk_backproject(ref, proj, mats, vs, org, fetch=fdk.FETCH_STAGE)
+        else:
+            fdk.fdk_backproject(ref, proj, mats, vs, org, fetch=fdk.FETCH_LDG, tile=plan.tile)
+        vol.zero_()
+        scans[i] = (ref, proj, mats, vs, org, vol)
+    plan.execute()
+    torch.cuda.synchronize()
+    for ref, *_rest, vol in scans:
+        equal = equal and bool(torch.equal(ref, vol))
+    tile = plan.tile
     plan.close()
+    del scans, g
+    torch.cuda.empty_cache()
+    return {"workload": label, "scans": len(cfgs), "views_total": sum(c.n_views for c in cfgs),
+            "updates_per_step": updates, "autotuned_tile": tile, "staged_scans": staged,
+            "batch_ms": ms_batch, "graph_replay_ms": ms_graph, "sequential_default_ms": ms_seq,
+            "batch_gups": updates / (ms_graph * 1e-3) / 1e9, "sequential_gups": updates / (ms_seq * 1e-3) / 1e9,
+            "speedup_vs_sequential": ms_seq / ms_graph, "bitwise_equal_to_sequential_calls": equal}
+
+
+def _batched_workloads(args):
+    import synth
+    return [
+        (f"uneven_{args.batch_scans}_scans", synth.batch_scan_configs(args.batch_scans),
+         f"{args.batch_scans} seeded scans: volumes 64..384 per axis, 120..496 views, detectors "
+         "640x480..1248x960, FP32 (each fills the GPU alone)"),
+        (f"small_{args.small_batch_scans}_scans", synth.small_batch_scan_configs(args.small_batch_scans),
+         f"{args.small_batch_scans} seeded small scans: volumes 32..96 per axis, 60..180 views, detectors "
+         "320x240..640x480, FP32 (each under-fills the GPU alone)"),
+    ]
+
+
+def run_batched(args):
+    """The batched form (one JSON line): an autotuned plan against
+    sequential default calls on 32 uneven scans and on many small ones."""
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    legs = [_batched_leg(args, cfgs, label, args.steps) for _key, cfgs, label in _batched_workloads(args)]
+    main = legs[0]
+    line = {
+        "metric": "GUp/s, scans of uneven size in one persistent launch (batched form)",
+        "value": main["batch_gups"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["graph_replay_ms"], "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": main["workload"]}, "legs": legs,
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _precision_leg(args) -> dict:
+    """The storage-precision form at 1024^3 x 496 views of 1248x960: FP32
+    storage (the default staged path) against BF16 and FP16 storage with FP32
+    interpolation and accumulation, each timed, with its error against the
+    FP32-storage GPU result on the whole volume and against the FP64 oracle
+    on a seeded 64^3 sub-block (given the same stored values, and the FP32
+    values)."""
+    import torch
+    import oracle
+    import synth
+    from paper_1401_3615_gb300 import fdk
+    cfg = synth.PRESETS["fdk1024"]
+    scan = synth.make_scan(cfg, device="cuda")
+    proj32, mats, vs, org = scan["proj"], scan["mats"], scan["voxel_size"], scan["origin"]
+    stream = torch.cuda.current_stream()
+    vol = torch.zeros((cfg.nz, cfg.ny, cfg.nx), dtype=torch.float32, device="cuda")
+    steps = max(1, min(args.steps, 3))
+
+    def timed(p):
+        for _ in range(2):
+            fdk.fdk_backproject(vol, p, mats, vs, org)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fdk.fdk_backproject(vol, p, mats, vs, org)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    out = {"workload": f"fdk1024: {cfg.nx}^3 FP32 volume, {cfg.n_views} views of {cfg.det_w}x{cfg.det_h}",
+           "fp32": {"ms_per_step": timed(proj32)}}
+    out["fp32"]["gups"] = cfg.updates / (out["fp32"]["ms_per_step"] * 1e-3) / 1e9
+    ref = torch.zeros_like(vol)
+    fdk.fdk_backproject(ref, proj32, mats, vs, org)
+    torch.cuda.synchronize()
+    peak = float(ref.abs().max())
+    rng = np.random.default_rng(1024)
+    n = np.array([cfg.nx, cfg.ny, cfg.nz])
+    lo = (n * 5) // 16
+    n0 = np.minimum(np.maximum(rng.integers(0, n - 64 + 1), lo), n - lo - 64)
+    zz, yy, xx = np.meshgrid(*(np.arange(n0[a], n0[a] + 64) for a in (2, 1, 0)), indexing="ij")
+    xyz = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)
+    threads = os.cpu_count() or 1
+    import concurrent.futures as cf
+    chunks = np.array_split(np.arange(len(xyz)), threads)
+
+    def orc(p):
+        with cf.ThreadPoolExecutor(threads) as ex:
+            return np.concatenate(list(ex.map(lambda idx: oracle.backproject_voxels(
+                p, mats, vs, org, xyz[idx]), chunks)))
+    o_exact = orc(proj32.cpu().numpy())
+    pk = float(np.abs(o_exact).max())
+    for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        p16 = proj32.to(dt)
+        ms = timed(p16)
+        low = torch.zeros_like(vol)
+        fdk.fdk_backproject(low, p16, mats, vs, org)
+        torch.cuda.synchronize()
+        diff = (low.double() - ref.double())
+        mse = float((diff ** 2).mean())
+        mx = float(diff.abs().max())
+        del diff
+        o_stored = orc(p16.float().cpu().numpy())
+        g = low[xyz[:, 2], xyz[:, 1], xyz[:, 0]].cpu().numpy().astype(np.float64)
+        out[name] = {"ms_per_step": ms, "gups": cfg.updates / (ms * 1e-3) / 1e9,
+                     "vs_fp32_storage_gpu_whole_volume": {
+                         "max_abs_over_peak": mx / peak,
+                         "psnr_db": float(10 * np.log10(peak ** 2 / mse)) if mse > 0 else float("inf")},
+                     "subblock_64_vs_oracle_same_stored_values": float(np.abs(g - o_stored).max()) / pk,
+                     "subblock_64_vs_oracle_fp32_values": float(np.abs(g - o_exact).max()) / pk,
+                     "storage_rounding_alone": float(np.abs(o_stored - o_exact).max()) / pk}
+        del low, p16
+    out["subblock_origin_voxel"] = [int(v) for v in n0]
+    del vol, ref, scan, proj32
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_micro(args):
@@ -741,6 +855,9 @@ def main():
     ap.add_argument("--batched", action="store_true", help="time the batched form instead")
     ap.add_argument("--micro", action="store_true", help="run the gather micro-benchmarks instead")
     ap.add_argument("--batch-scans", type=int, default=32)
+    ap.add_argument("--small-batch-scans", type=int, default=128)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form key of the line")
+    ap.add_argument("--no-precision", action="store_true", help="skip the storage-precision key of the line")
     ap.add_argument("--views", type=int, default=0, help="override the view count (profiling)")
     ap.add_argument("--proj-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="projection storage type (the storage-precision form)")

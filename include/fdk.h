@@ -307,7 +307,20 @@ typedef struct fdk_batch_plan_t *fdk_batch_plan;
  * is used.  With opts->autotune = 1 it times the tile variants 0, 2..5 and 7
  * on the batch (writing into a scratch volume, never into the scans'
  * volumes) and keeps the fastest; otherwise opts->tile (0..5 or 7) is used.
- * opts->proj_dtype must be FDK_F32 and opts->fetch AUTO or LDG.
+ * opts->proj_dtype must be FDK_F32.
+ *
+ * Fetch path per scan: with opts->fetch = FDK_FETCH_AUTO (the default) a
+ * scan takes the staged path where fdk_backproject's AUTO would (W a
+ * multiple of 4, a 16-byte aligned base, footprints that fit the stages),
+ * on its own 16 x 16 x 16 tiles, for up to 32 scans of the batch, provided
+ * the plan's tile variant has 16 x 16 threads (0, 5, 7); the other scans
+ * take the global-load path on the plan's tile variant.  The autotuner times
+ * the plan with and without staging those scans (one persistent kernel runs
+ * both paths, at the staged path's 3 CTAs per SM, which can cost the
+ * global-load scans more than staging saves) and keeps the faster.  FDK_FETCH_LDG: every scan takes the global-load
+ * path.  fdk_batch_plan_scan_fetch tells which path a scan takes.  A staged
+ * scan's bounded waits are reported by fdk_device_status(), as for
+ * fdk_backproject.
  */
 FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans,
                                          int32_t n_scans, const fdk_opts *opts);
@@ -317,8 +330,8 @@ FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *s
  * NULL = legacy default stream): a reset of the plan's work counter and one
  * persistent kernel in which CTAs take (scan, tile) items from that counter
  * until none are left.  Every volume is accumulated (+=) exactly as by
- * fdk_backproject with FDK_FETCH_LDG and the plan's tile variant, bit for
- * bit.  It allocates nothing and does not synchronise.  Executions of one plan must not
+ * fdk_backproject, bit for bit: with FDK_FETCH_STAGE for the staged scans,
+ * with FDK_FETCH_LDG and the plan's tile variant for the others.  It allocates nothing and does not synchronise.  Executions of one plan must not
  * overlap on the GPU (they share the counter); the plan's device must be
  * current.
  */
@@ -327,6 +340,11 @@ FDK_API fdk_status fdk_batch_plan_execute(fdk_batch_plan plan, void *stream);
 /* The tile variant a plan uses (the autotuner's pick when it ran).  A service
  * call of the batched form; the paper has no counterpart. */
 FDK_API fdk_status fdk_batch_plan_tile(fdk_batch_plan plan, int32_t *tile);
+
+/* The fetch path scan `scan` of a plan takes: FDK_FETCH_STAGE or
+ * FDK_FETCH_LDG, in *fetch.  A service call of the batched form; the paper has
+ * no counterpart. */
+FDK_API fdk_status fdk_batch_plan_scan_fetch(fdk_batch_plan plan, int32_t scan, int32_t *fetch);
 
 /* Free a plan's device memory.  No execution of it may still be in flight.
  * A service call; the paper has no counterpart. */

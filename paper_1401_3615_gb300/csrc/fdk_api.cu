@@ -371,9 +371,10 @@ static EncodeTiledFn tmap_encoder()
     return fn;
 }
 
-// One map per box width over the pass's nv FP32 images (W x H x nv; the
-// row and image strides are multiples of 16 bytes because W % 4 == 0).
-static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
+// One map per box width (maps[0..kNumBoxW)) over nv FP32 images at base
+// (W x H x nv; the row and image strides are multiples of 16 bytes because
+// W % 4 == 0).
+static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int W, int H, int nv)
 {
     EncodeTiledFn enc = tmap_encoder();
     const cuuint64_t gdim[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nv};
@@ -381,7 +382,7 @@ static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
     const cuuint32_t estride[3] = {1, 1, 1};
     for (int m = 0; m < kNumBoxW; ++m) {
         const cuuint32_t box[3] = {(cuuint32_t)box_width(m), (cuuint32_t)kBoxRows, 1};
-        CUresult r = enc(&a.tmap[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.proj), gdim,
+        CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), gdim,
                          gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -390,6 +391,12 @@ static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
         }
     }
     return FDK_OK;
+}
+
+// The pass's maps in the kernel parameters.
+static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
+{
+    return encode_stage_maps_at(a.tmap, a.proj, W, H, nv);
 }
 
 // Adjoint warp patches (voxels along x) for views whose rays run mostly along
@@ -1301,6 +1308,9 @@ struct fdk_batch_plan_t {
     int *d_tile_start = nullptr;
     int *d_counter = nullptr;
     std::vector<fdk::ScanDesc> h_descs;
+    std::unique_ptr<fdk::BatchLaunch> launch;   // kernel arguments, staged scans' tensor maps included
+    std::vector<int> stage_slot;     // per scan: its tensor maps' slot if it can be staged, else -1
+    int n_stageable = 0;
 };
 
 namespace fdk {
@@ -1316,7 +1326,10 @@ static int plan_tile_start(const fdk_batch_plan_t *p, int tile, std::vector<int>
         ts[s] = (int)acc;
         const Geom &g = p->h_descs[2 * s].g;
         const bool any = p->h_descs[2 * s].n_views + p->h_descs[2 * s + 1].n_views > 0;
-        if (any) acc += (long long)((g.nx + bx - 1) / bx) * ((g.ny + by - 1) / by) * ((g.nz + r - 1) / r);
+        // staged scans are cut into the staged path's tiles
+        const bool staged = p->h_descs[2 * s].tmap_slot >= 0;
+        const int sx = staged ? kStageTileXY : bx, sy = staged ? kStageTileXY : by, sz = staged ? kStageTileZ : r;
+        if (any) acc += (long long)((g.nx + sx - 1) / sx) * ((g.ny + sy - 1) / sy) * ((g.nz + sz - 1) / sz);
     }
     ts[p->n_scans] = (int)acc;
     return acc > INT32_MAX ? -1 : (int)acc;
@@ -1342,17 +1355,33 @@ static fdk_status plan_launch(fdk_batch_plan_t *p, cudaStream_t s)
         cudaGetLastError();
         return fail(FDK_ERR_CUDA, "batch: counter reset failed");
     }
-    BatchLaunch b;
-    b.descs = p->d_descs;
-    b.tile_start = p->d_tile_start;
-    b.counter = p->d_counter;
-    b.n_scans = p->n_scans;
+    BatchLaunch &b = *p->launch;
     b.total = p->total;
+    b.wait_limit = consumer_wait_limit();
     return launch_batched(b, p->tile, p->fidx, s);
 }
 
-// Time the tile variants on the batch with every volume redirected to one
-// scratch buffer (the scans' volumes are never written), keep the fastest.
+// Tile variants whose CTAs are 16 x 16 threads, as the staged scans' are:
+// the only ones a plan with staged scans can run.
+static bool tile_is_16x16(int tile)
+{
+    int bx, by, r;
+    batched_tile_dims(tile, &bx, &by, &r);
+    return bx == kStageTileXY && by == kStageTileXY;
+}
+
+// Stage the scans that can be staged (on) or none of them (off).  The caller
+// uploads the descriptors.
+static void plan_set_staging(fdk_batch_plan_t *p, bool on)
+{
+    for (int s = 0; s < p->n_scans; ++s)
+        p->h_descs[2 * s].tmap_slot = p->h_descs[2 * s + 1].tmap_slot = on ? p->stage_slot[s] : -1;
+    p->launch->n_staged = on ? p->n_stageable : 0;
+}
+
+// Time the tile variants, with and without the staged path for the scans
+// that can take it, on the batch with every volume redirected to one scratch
+// buffer (the scans' volumes are never written); keep the fastest.
 static fdk_status plan_autotune(fdk_batch_plan_t *p)
 {
     size_t vmax = 0;
@@ -1365,30 +1394,37 @@ static fdk_status plan_autotune(fdk_batch_plan_t *p)
         cudaGetLastError();
         return fail(FDK_ERR_OOM, "autotune: scratch volume allocation failed");
     }
-    std::vector<ScanDesc> tuned = p->h_descs;
-    for (auto &d : tuned) d.vol = scratch;
-    cudaMemcpy(p->d_descs, tuned.data(), sizeof(ScanDesc) * tuned.size(), cudaMemcpyHostToDevice);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int cands[] = {0, 2, 3, 4, 5, 7};
     int best = 0;
+    bool best_staged = false;
     float best_ms = 3.0e38f;
     fdk_status st = FDK_OK;
-    for (int c : cands) {
-        if ((st = plan_set_tile(p, c))) break;
-        if ((st = plan_launch(p, 0))) break;            // warm-up
-        cudaEventRecord(e0, 0);
-        for (int rep = 0; rep < 2 && st == FDK_OK; ++rep) st = plan_launch(p, 0);
-        cudaEventRecord(e1, 0);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = fail(FDK_ERR_CUDA, "autotune: timing failed"); }
-        if (st) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = c; }
+    for (int staged = 0; staged < 2 && st == FDK_OK; ++staged) {
+        if (staged && p->n_stageable == 0) break;
+        plan_set_staging(p, staged != 0);
+        std::vector<ScanDesc> tuned = p->h_descs;
+        for (auto &d : tuned) d.vol = scratch;
+        cudaMemcpy(p->d_descs, tuned.data(), sizeof(ScanDesc) * tuned.size(), cudaMemcpyHostToDevice);
+        for (int c : cands) {
+            if (staged && !tile_is_16x16(c)) continue;
+            if ((st = plan_set_tile(p, c))) break;
+            if ((st = plan_launch(p, 0))) break;            // warm-up
+            cudaEventRecord(e0, 0);
+            for (int rep = 0; rep < 2 && st == FDK_OK; ++rep) st = plan_launch(p, 0);
+            cudaEventRecord(e1, 0);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = fail(FDK_ERR_CUDA, "autotune: timing failed"); }
+            if (st) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = c; best_staged = staged != 0; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    plan_set_staging(p, best_staged);
     cudaMemcpy(p->d_descs, p->h_descs.data(), sizeof(ScanDesc) * p->h_descs.size(), cudaMemcpyHostToDevice);
     cudaDeviceSynchronize();
     cudaFree(scratch);
@@ -1414,7 +1450,7 @@ fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, in
     if (autotune != 0 && autotune != 1) return fail(FDK_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o.proj_dtype != FDK_F32) return fail(FDK_ERR_INVALID_ARG, "batches take FP32 projections");
     if (o.fetch != FDK_FETCH_AUTO && o.fetch != FDK_FETCH_LDG)
-        return fail(FDK_ERR_INVALID_ARG, "batches use the LDG fetch path");
+        return fail(FDK_ERR_INVALID_ARG, "batches take FDK_FETCH_AUTO (staged where it pays) or FDK_FETCH_LDG");
     if (o.matrices_on_device) return fail(FDK_ERR_INVALID_ARG, "batches take host matrices");
     if (o.tile == 6 || o.tile > 7) return fail(FDK_ERR_INVALID_ARG, "batches take tile variants 0..5 and 7");
     if (n_scans < 1 || !scans) return fail(FDK_ERR_INVALID_ARG, "need at least one scan");
@@ -1479,8 +1515,40 @@ fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, in
                 ++cnt;
             }
             d.n_views = cnt;
+            d.tmap_slot = -1;
             at += cnt;
         }
+    }
+    // Scans that can take the staged path (where fdk_backproject's AUTO
+    // would, on 16 x 16 x 16 tiles): their tensor maps go into the kernel
+    // parameters.  They are staged when the plan's tile variant has 16 x 16
+    // threads, or, with the autotuner, when staging them measures faster.
+    p->launch.reset(new BatchLaunch());
+    BatchLaunch &L = *p->launch;
+    memset(&L, 0, sizeof L);
+    p->stage_slot.assign(n_scans, -1);
+    const bool may_stage = o.fetch == FDK_FETCH_AUTO && (autotune || tile_is_16x16(o.tile)) && tmap_encoder();
+    for (int s = 0; s < n_scans && may_stage; ++s) {
+        const fdk_scan &sc = scans[s];
+        const Geom &g = p->h_descs[2 * s].g;
+        if (p->n_stageable >= kMaxStagedScans || sc.n_views < 1 || g.W % 4 != 0 ||
+            ((uintptr_t)sc.projections) % 16 != 0 || !stage_pays(g, sc.matrices, sc.n_views))
+            continue;
+        const int slot = p->n_stageable++;
+        if ((st = encode_stage_maps_at(L.tmaps + slot * kNumBoxW, sc.projections, g.W, g.H, sc.n_views))) {
+            cudaFree(p->buf);
+            return st;
+        }
+        p->stage_slot[s] = slot;
+    }
+    plan_set_staging(p.get(), true);
+    L.descs = p->d_descs;
+    L.tile_start = p->d_tile_start;
+    L.counter = p->d_counter;
+    L.n_scans = n_scans;
+    if (p->n_stageable > 0 && (st = err_word(p->dev, &L.err))) {
+        cudaFree(p->buf);
+        return st;
     }
     cudaError_t e = cudaMemcpy(base + off_mats, hm.data(), sizeof(float) * hm.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + off_vidx, hv.data(), sizeof(int) * hv.size(), cudaMemcpyHostToDevice);
@@ -1515,6 +1583,15 @@ fdk_status fdk_batch_plan_tile(fdk_batch_plan plan, int32_t *tile)
     g_err[0] = 0;
     if (!plan || !tile) return fail(FDK_ERR_INVALID_ARG, "null argument");
     *tile = plan->tile;
+    return FDK_OK;
+}
+
+fdk_status fdk_batch_plan_scan_fetch(fdk_batch_plan plan, int32_t scan, int32_t *fetch)
+{
+    g_err[0] = 0;
+    if (!plan || !fetch) return fail(FDK_ERR_INVALID_ARG, "null argument");
+    if (scan < 0 || scan >= plan->n_scans) return fail(FDK_ERR_INVALID_ARG, "scan index out of range");
+    *fetch = plan->h_descs[2 * (size_t)scan].tmap_slot >= 0 ? FDK_FETCH_STAGE : FDK_FETCH_LDG;
     return FDK_OK;
 }
 

@@ -1,269 +1,22 @@
-// Staged fetch path of the back-projection (Listing 1, Sec. IV): for every
-// (tile, view) whose footprint fits, the pixel box holding all of the tile's
-// taps is copied from global memory into shared memory by the tensor-memory
-// accelerator (cp.async.bulk.tensor, completion on an mbarrier) and the four
-// taps of each voxel are read from there.  The copy reads zeros outside the
-// image, so boundary tiles need no bounds checks (the effect of the paper's
-// zero-padded projection copy, Sec. VI, without a copy in global memory).
-//
-// Why: on the global-load path the L1 data pipe is the binding unit, and
-// about a third of its cycles are sector fills of the footprints from L2.
-// A bulk copy moves the same footprint in full 128-byte lines.
-//
-// Pipeline per CTA: kStages shared-memory stages.  Every thread waits on the
-// stage's mbarrier and computes the view; after a CTA barrier (the stage is
-// then free) warp 0 issues the copy of the staged view kStages further on
-// into it, one 8-row box per lane, so the next view's copy is in flight
-// while the CTA computes.
-// Each thread owns a z-run of 16 voxels, so the per-view barrier is shared
-// by 16 updates per thread (8 per thread measured 10% slower, 24 slower
-// still).  (A barrier-free variant, in which the last warp done with a stage
-// refills it, measured 12% slower: its warps spin on the mbarriers instead.)
-// Every wait is bounded; a wait that gives up sets *a.err, thread 0 drains
-// the copies still in flight (again bounded) and the CTA returns without
-// writing its tile.  The taps are read with 32-bit shared addresses.
-#include "fdk_bp_kernel.cuh"
+// The plain staged back-projection: one CTA per 16 x 16 x 16 tile (the
+// pipeline itself is in fdk_stage.cuh).
+#include "fdk_stage.cuh"
 
 namespace fdk {
-
-constexpr int kStages = 2;
-constexpr int kStageChunk = 64;          // views per table chunk on this path
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Bounded wait for the phase with the given parity of the mbarrier at bar:
-// at most `limit` polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
-{
-    for (long long it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// Copy the box of table entry lv (view v0 + lv of the pass) into stage st.
-// Called by one thread.
-__device__ __forceinline__ void stage_issue(const BpArgs &a, int v0, int lv, const int4 *sbox,
-                                            float *stages, uint32_t full0, unsigned st)
-{
-    // order the CTA's reads of this stage (before the caller's barrier)
-    // before the asynchronous copy that overwrites it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const int4 b = sbox[lv];                       // (x0, j0, m, rows8)
-    const int BW = box_width(b.z);
-    const uint32_t bar = full0 + 8u * st;
-    const uint32_t bytes = (uint32_t)(b.w * kBoxRows * BW) * 4u;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"(bytes) : "memory");
-    const uint32_t dst = smem_addr(stages + (size_t)st * kStageFloats);
-    const CUtensorMap *map = &a.tmap[b.z];
-    const int img = a.vidx[v0 + lv];
-    for (int r = 0; r < b.w; ++r) {
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];"
-            :: "r"(dst + (uint32_t)(r * kBoxRows * BW) * 4u), "l"(map), "r"(b.x),
-               "r"(b.y + r * kBoxRows), "r"(img), "r"(bar)
-            : "memory");
-    }
-}
-
-// Shared-memory loads of the words at a 32-bit shared address and the one
-// after it (the offset in the instruction, not in a register).  Volatile, so
-// they stay after the (volatile) mbarrier wait that makes the stage's data
-// visible.
-__device__ __forceinline__ float lds(uint32_t addr)
-{
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ float lds_next(uint32_t addr)
-{
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1+4];" : "=f"(v) : "r"(addr));
-    return v;
-}
-
-// Staged view: the taps come from the stage's box, BW = e.o.w pixels wide,
-// whose cell (U, V) sits at index e.o.z - 2^23.  No bounds checks: the box
-// holds every tap of the tile, with zeros where it extends past the image.
-// Each f32x2 pair holds one quantity for two z neighbours, so every packed
-// operation finds its operands in place.
-template <int R>
-__device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e, float dxf, float dyf,
-                                            const float *stage)
-{
-    const float2 BU = f2(fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x)));
-    const float2 BV = f2(fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y)));
-    const float2 BW = f2(fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x)));
-    const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
-    const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
-    const float2 PITCH = f2(e.o.w), OZ = f2(e.o.z);
-    // 32-bit shared addresses of the tap rows j and j + 1, with the index
-    // magic folded into the bases
-    const uint32_t sbase = smem_addr(stage) - (kIndexBits << 2);
-    const uint32_t sbase1 = sbase + ((uint32_t)(int)e.o.w << 2);
-#pragma unroll
-    for (int r = 0; r < R; r += 2) {
-        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
-        const float2 wl = __ffma2_rn(RF, GW, BW);
-        const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
-        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
-        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
-        const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
-        const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
-        const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
-        const float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OZ);
-        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
-        const uint32_t a0 = sbase + o0, a1 = sbase + o1, b0 = sbase1 + o0, b1 = sbase1 + o1;
-        const float2 p00 = f2(lds(a0), lds(a1)), p10 = f2(lds_next(a0), lds_next(a1));
-        const float2 p01 = f2(lds(b0), lds(b1)), p11 = f2(lds_next(b0), lds_next(b1));
-        const float2 lo = __ffma2_rn(au, __ffma2_rn(p00, NEG, p10), p00);
-        const float2 hi = __ffma2_rn(au, __ffma2_rn(p01, NEG, p11), p01);
-        const float2 val = __ffma2_rn(bv, __ffma2_rn(lo, NEG, hi), lo);
-        const float2 s2 = __ffma2_rn(val, __fmul2_rn(iw, iw), f2(acc[r], acc[r + 1]));
-        acc[r] = s2.x;
-        acc[r + 1] = s2.y;
-    }
-}
 
 template <int BX, int BY, int WX, int R, int MINB, bool FIDX>
 __global__ void __launch_bounds__(BX * BY, MINB)
 fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
 {
-    static_assert(32 % WX == 0 && BX % WX == 0 && BY % (32 / WX) == 0, "warp tiling");
-    static_assert(R % 2 == 0, "z-run must be even (voxel pairs)");
-    constexpr int KCHUNK = kStageChunk;
-    __shared__ ViewEntry tab[KCHUNK];
-    __shared__ int4 sbox[KCHUNK];
-    __shared__ unsigned char cls[KCHUNK];
-    __shared__ unsigned short act[KCHUNK];
-    __shared__ unsigned short stg[KCHUNK];       // table entries of the staged views, in order
-    __shared__ int n_act, n_stg;
-    __shared__ __align__(8) unsigned long long full[kStages];
-    __shared__ unsigned nissue[kStages];         // copies issued into each stage so far
+    __shared__ StageTables t;
+    __shared__ __align__(8) StageBarriers sb;
     extern __shared__ __align__(1024) float stages[];
-
-    constexpr int WY = 32 / WX;
-    constexpr int WPX = BX / WX;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int lx = (warp % WPX) * WX + (lane % WX);
-    const int ly = (warp / WPX) * WY + (lane / WX);
-    const float dxf = (float)(lx - BX / 2), dyf = (float)(ly - BY / 2);
     // CTAs are scheduled in blockIdx.x order: walking along the rays keeps
     // the resident CTAs' footprints overlapping, so their boxes hit in L2
     const int tx = a.walk_y ? blockIdx.y : blockIdx.x, ty = a.walk_y ? blockIdx.x : blockIdx.y;
-    const int x0 = tx * BX, y0 = ty * BY, z0 = blockIdx.z * R;
-    const int W = a.g.W, H = a.g.H;
-    const float *proj = static_cast<const float *>(a.proj);
-    const uint32_t full0 = smem_addr(full);
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full0 + 8u * s) : "memory");
-            nissue[s] = 0;
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-
-    float acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0.0f;
-
-    unsigned base = 0;        // staged views of earlier chunks (uniform)
-    for (int v0 = 0; v0 < a.n_views; v0 += KCHUNK) {
-        const int nv = min(KCHUNK, a.n_views - v0);
-        build_view_table<BX, BY, R, BpArgs, true>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act,
-                                                  nullptr, nullptr, sbox);
-        const int n = n_act;
-        if (warp == 0) {
-            // compact the staged views, in view order
-            int count = 0;
-            for (int q0 = 0; q0 < n; q0 += 32) {
-                const int q = q0 + lane;
-                const bool is_st = q < n && (act[q] >> 10) == kStaged;
-                const unsigned m = __ballot_sync(0xffffffffu, is_st);
-                if (is_st) stg[count + __popc(m & ((1u << lane) - 1u))] = act[q] & 1023;
-                count += __popc(m);
-            }
-            if (lane == 0) n_stg = count;
-            __syncwarp();
-            if (lane == 0) {
-                // the first copies of the chunk
-                for (int k = 0; k < kStages && k < count; ++k) {
-                    const unsigned st = (base + k) % kStages;
-                    stage_issue(a, v0, stg[k], sbox, stages, full0, st);
-                    ++nissue[st];
-                }
-            }
-        }
-        __syncthreads();
-        const unsigned ns = (unsigned)n_stg;
-        unsigned kst = 0;     // staged views of this chunk consumed so far (uniform)
-        for (int q = 0; q < n; ++q) {
-            const int ev = act[q];
-            const int lv = ev & 1023, c = ev >> 10;
-            if (c == kStaged) {
-                const unsigned slot = base + kst;
-                const unsigned st = slot % kStages;
-                const bool ok = mbar_wait(full0 + 8u * st, (slot / kStages) & 1u, a.wait_limit);
-                const ViewEntry e = tab[lv];
-                view_staged<R>(acc, e, dxf, dyf, stages + (size_t)st * kStageFloats);
-                ++kst;
-                if (!__syncthreads_and(ok)) {
-                    if (tid == 0) {
-                        atomicOr(a.err, 1u);
-                        // drain with the full limit: no copy may still be
-                        // writing this CTA's shared memory when it exits
-                        for (int s = 0; s < kStages; ++s)
-                            if (nissue[s] > 0) mbar_wait(full0 + 8u * s, (nissue[s] - 1) & 1u, kWaitLimit);
-                    }
-                    return;
-                }
-                if (tid == 0) {
-                    const unsigned nk = kst - 1 + kStages;
-                    if (nk < ns) {
-                        stage_issue(a, v0, stg[nk], sbox, stages, full0, st);
-                        ++nissue[st];
-                    }
-                }
-                continue;
-            }
-            const ViewEntry e = tab[lv];
-            const float *img = proj + (long long)a.vidx[v0 + lv] * a.plane;
-            if (c == kInterior) view_interior_ldg<R, float, FIDX>(acc, e, dxf, dyf, img, W);
-            else if (c == kBoundary) view_checked_ldg<R, float, false>(acc, e, dxf, dyf, img, W, H);
-            else view_checked_ldg<R, float, true>(acc, e, dxf, dyf, img, W, H);
-        }
-        base += ns;
-        __syncthreads();   // the next chunk overwrites the table
-    }
-
-    const int x = x0 + lx, y = y0 + ly;
-    if (x < a.g.nx && y < a.g.ny) {
-        const long long sxy = (long long)a.g.nx * a.g.ny;
-        float *col = a.vol + (long long)y * a.g.nx + x;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int z = z0 + r;
-            if (z < a.g.nz) col[z * sxy] += acc[r];
-        }
-    }
+    stage_init(sb);
+    stage_tile<BX, BY, WX, R, FIDX>(a, a.tmap, a.err, a.wait_limit, tx * BX, ty * BY, blockIdx.z * R, t, sb,
+                                    stages);
 }
 
 template <int WX, bool FIDX>

@@ -88,17 +88,28 @@ struct ScanDesc {
     const float *mats;         // unused (always nullptr)
     const int *vidx;           // image index of each view of the group
     int n_views;               // views in this group
-    int pad;
+    int tmap_slot;             // staged scans: index of the scan's tensor maps in the launch; -1: LDG
 };
 
-// Arguments of one batched launch (device pointers).
+// Scans of one batch that can take the staged path (their tensor maps travel
+// in the kernel parameters, kNumBoxW per scan).
+constexpr int kMaxStagedScans = 32;
+
+// Arguments of one batched launch (device pointers, plus the staged scans'
+// tensor maps).  About 28.7 KB, under the 32 KB kernel-parameter limit.
 struct BatchLaunch {
     const ScanDesc *descs;     // 2 per scan: views along x, views along y
     const int *tile_start;     // n_scans + 1 prefix counts of (scan, tile) items
     int *counter;              // work counter, zeroed before the launch
+    unsigned *err;             // device word set when a bounded wait gives up (staged scans)
+    long long wait_limit;      // polls before a consumer's wait for a staged view gives up
     int n_scans;
     int total;                 // work items
+    int n_staged;              // scans with tensor maps (tmap_slot >= 0)
+    CUtensorMap tmaps[kMaxStagedScans * kNumBoxW];   // one per box width per staged scan,
+                                                     // over the scan's W x H x n_views images
 };
+static_assert(sizeof(BatchLaunch) <= 32764, "kernel parameter block limit");
 
 enum TileClass : int { kSkip = 0, kInterior = 1, kBoundary = 2, kGeneral = 3, kStaged = 4 };
 
@@ -126,6 +137,8 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
                          int N, unsigned *err, cudaStream_t stream);
 fdk_status launch_batched(const BatchLaunch &b, int tile, bool fidx, cudaStream_t stream);
 void batched_tile_dims(int tile, int *bx, int *by, int *r);
+// Tile of a staged scan in a batch: the staged path's 16 x 16 x 16.
+constexpr int kStageTileXY = 16, kStageTileZ = 16;
 size_t quad_elem_size(int dtype);
 fdk_status launch_make_quads(const void *proj, void *quads, int n, int W, int H, int dtype,
                              cudaStream_t stream);

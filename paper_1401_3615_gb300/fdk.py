@@ -84,6 +84,8 @@ def _load():
             lib.fdk_batch_plan_execute.restype = ctypes.c_int
             lib.fdk_batch_plan_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
             lib.fdk_batch_plan_tile.restype = ctypes.c_int
+            lib.fdk_batch_plan_scan_fetch.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+            lib.fdk_batch_plan_scan_fetch.restype = ctypes.c_int
             lib.fdk_batch_plan_destroy.argtypes = [vp]
             lib.fdk_batch_plan_destroy.restype = None
             lib.fdk_backproject_batched.argtypes = [sp, ctypes.c_int32, op]
@@ -363,11 +365,12 @@ class BatchPlan:
     """fdk_batch_plan_create / _execute / _tile / _destroy.  The tensors of
     every scan must outlive the plan."""
 
-    def __init__(self, scans, *, tile: int = 0, autotune: bool = False):
+    def __init__(self, scans, *, tile: int = 0, autotune: bool = False, fetch: int = FETCH_AUTO):
         arr, keep = _scan_array(scans)
         o = fdk_opts()
         o.tile = tile
         o.autotune = 1 if autotune else 0
+        o.fetch = fetch
         h = ctypes.c_void_p()
         lib = _load()
         self._tensors = [t for sc in scans for t in (sc[0], sc[1])]
@@ -382,6 +385,12 @@ class BatchPlan:
         t = ctypes.c_int32(0)
         _check(self._lib.fdk_batch_plan_tile(self._h, ctypes.byref(t)))
         return int(t.value)
+
+    def scan_fetch(self, scan: int) -> int:
+        """FETCH_STAGE or FETCH_LDG: the fetch path the plan uses for scan ``scan``."""
+        f = ctypes.c_int32(0)
+        _check(self._lib.fdk_batch_plan_scan_fetch(self._h, int(scan), ctypes.byref(f)))
+        return int(f.value)
 
     def execute(self, stream=None):
         with _on(*self._tensors):
@@ -400,15 +409,16 @@ class BatchPlan:
             pass
 
 
-def fdk_batch_plan_create(scans, *, tile: int = 0, autotune: bool = False) -> BatchPlan:
-    return BatchPlan(scans, tile=tile, autotune=autotune)
+def fdk_batch_plan_create(scans, *, tile: int = 0, autotune: bool = False, fetch: int = FETCH_AUTO) -> BatchPlan:
+    return BatchPlan(scans, tile=tile, autotune=autotune, fetch=fetch)
 
 
-def fdk_backproject_batched(scans, *, tile: int = 0, stream=None):
+def fdk_backproject_batched(scans, *, tile: int = 0, fetch: int = FETCH_AUTO, stream=None):
     """One-shot batch: create a plan, execute it, synchronise, destroy."""
     arr, keep = _scan_array(scans)
     o = fdk_opts()
     o.tile = tile
+    o.fetch = fetch
     lib = _load()
     with _on(*[t for sc in scans for t in (sc[0], sc[1])]):
         o.stream = stream if isinstance(stream, int) else (stream or torch.cuda.current_stream()).cuda_stream

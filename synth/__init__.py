@@ -36,7 +36,7 @@ import torch
 __all__ = [
     "ScanConfig", "PRESETS", "preset", "geometry", "phantom", "projections",
     "volume_geometry", "make_scan", "gaussian_volume", "gaussian_projections",
-    "batch_scan_configs", "from_column_major",
+    "batch_scan_configs", "small_batch_scan_configs", "from_column_major",
 ]
 
 
@@ -293,6 +293,26 @@ def batch_scan_configs(n_scans: int = 32, seed: int = 505) -> list:
         views = int(rng.integers(120, 497))
         w = int(rng.integers(640, 1249))
         h = int(rng.integers(480, 961))
+        pix = 0.308 * 1248.0 / w
+        out.append(ScanConfig(nx=nx, ny=ny, nz=nz, voxel=256.0 / max(nx, ny, nz),
+                              n_views=views, det_w=w, det_h=h, pixel=pix,
+                              seed=int(rng.integers(1, 2 ** 31))))
+    return out
+
+
+def small_batch_scan_configs(n_scans: int = 128, seed: int = 606) -> list:
+    """Seeded small scans for the batched form, each too small to fill the GPU
+    on its own: volumes 32..96 voxels per axis (non-cubic), 60..180 views,
+    detectors from 320x240 to 640x480 with the pixel pitch scaled so each
+    spans the field of the 1248x960 / 0.308 mm panel; the volume stays a
+    256 mm cube."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scans):
+        nx, ny, nz = (int(v) for v in rng.integers(32, 97, size=3))
+        views = int(rng.integers(60, 181))
+        w = int(rng.integers(320, 641))
+        h = int(rng.integers(240, 481))
         pix = 0.308 * 1248.0 / w
         out.append(ScanConfig(nx=nx, ny=ny, nz=nz, voxel=256.0 / max(nx, ny, nz),
                               n_views=views, det_w=w, det_h=h, pixel=pix,

@@ -183,6 +183,16 @@ def test_named_workloads_and_batch_sizes():
         assert abs(c.det_w * c.pixel - 1248 * 0.308) < 1e-9        # the same detector field
     assert len({(c.nx, c.ny, c.nz) for c in scans}) == 32
     assert any(len({c.nx, c.ny, c.nz}) > 1 for c in scans)          # non-cubic volumes present
+    small = synth.small_batch_scan_configs(128)
+    assert len(small) == 128
+    for c in small:
+        assert all(32 <= d <= 96 for d in (c.nx, c.ny, c.nz))
+        assert 60 <= c.n_views <= 180
+        assert 320 <= c.det_w <= 640 and 240 <= c.det_h <= 480
+        assert abs(max(c.nx, c.ny, c.nz) * c.voxel - 256.0) < 1e-9
+        assert abs(c.det_w * c.pixel - 1248 * 0.308) < 1e-9
+    # each scan alone under-fills the GPU: fewer 16 x 16 x 8 tiles than 152 SMs x 4 CTAs
+    assert max((c.nx + 15) // 16 * ((c.ny + 15) // 16) * ((c.nz + 7) // 8) for c in small) < 152 * 4
 
 
 def test_same_seed_same_scan():
