@@ -374,15 +374,16 @@ static EncodeTiledFn tmap_encoder()
 // One map per box width (maps[0..kNumBoxW)) over nv FP32 images at base
 // (W x H x nv; the row and image strides are multiples of 16 bytes because
 // W % 4 == 0).
-static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int W, int H, int nv)
+static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int W, int H, int nv, int nh = 1)
 {
     EncodeTiledFn enc = tmap_encoder();
     const cuuint64_t gdim[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nv};
     const cuuint64_t gstride[2] = {(cuuint64_t)W * 4u, (cuuint64_t)W * (cuuint64_t)H * 4u};
     const cuuint32_t estride[3] = {1, 1, 1};
-    for (int m = 0; m < kNumBoxW; ++m) {
-        const cuuint32_t box[3] = {(cuuint32_t)box_width(m), (cuuint32_t)kBoxRows, 1};
-        CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), gdim,
+    for (int q = 0; q < kNumBoxW * nh; ++q) {
+        const int m = q / nh, h = q % nh;
+        const cuuint32_t box[3] = {(cuuint32_t)box_width(m), (cuuint32_t)(kBoxRows << h), 1};
+        CUresult r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), gdim,
                          gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -396,7 +397,7 @@ static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int 
 // The pass's maps in the kernel parameters.
 static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
 {
-    return encode_stage_maps_at(a.tmap, a.proj, W, H, nv);
+    return encode_stage_maps_at(a.tmap, a.proj, W, H, nv, kNumBoxH);
 }
 
 // Adjoint warp patches (voxels along x) for views whose rays run mostly along

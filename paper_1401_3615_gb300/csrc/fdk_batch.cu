@@ -23,7 +23,7 @@ __device__ __noinline__ bool batch_stage_tile(const ScanDesc &d, const CUtensorM
                                               long long wait_limit, int x0, int y0, int z0, StageTables &t,
                                               StageBarriers &sb, float *stages)
 {
-    return stage_tile<kStageTileXY, kStageTileXY, WX, kStageTileZ, FIDX>(d, maps, err, wait_limit, x0, y0, z0,
+    return stage_tile<kStageTileXY, kStageTileXY, WX, kStageTileZ, FIDX, 1>(d, maps, err, wait_limit, x0, y0, z0,
                                                                          t, sb, stages);
 }
 

@@ -146,13 +146,21 @@ __device__ __forceinline__ void view_interior_ldg(float (&acc)[R], const ViewEnt
         FIDX ? (unsigned long long)img - (unsigned long long)kIndexBits * sizeof(T)
              : (unsigned long long)img;
     const unsigned long long row1 = row0 + (unsigned long long)W * sizeof(T);
+    // (u', v', w) of the run's first two voxels, then stepped two voxels at a
+    // time (the steps 2 g are exact)
+    const float2 RF0 = f2((float)(-R / 2), (float)(1 - R / 2));
+    float2 wl = __ffma2_rn(RF0, GW, BW), uq = __ffma2_rn(RF0, GU, BU), vq = __ffma2_rn(RF0, GV, BV);
+    const float2 G2W = __fadd2_rn(GW, GW), G2U = __fadd2_rn(GU, GU), G2V = __fadd2_rn(GV, GV);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
-        const float2 wl = __ffma2_rn(RF, GW, BW);
+        if (r > 0) {
+            wl = __fadd2_rn(wl, G2W);
+            uq = __fadd2_rn(uq, G2U);
+            vq = __fadd2_rn(vq, G2V);
+        }
         const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
-        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
-        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 u = __fmul2_rn(uq, iw);
+        const float2 v = __fmul2_rn(vq, iw);
         const float2 tu = __fadd2_rd(u, M), tv = __fadd2_rd(v, M);
         const float2 flu = __fadd2_rn(tu, NM), flv = __fadd2_rn(tv, NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
@@ -196,12 +204,21 @@ __device__ __forceinline__ void view_checked_ldg(float (&acc)[R], const ViewEntr
     // cell-relative clamp range keeping every int exact; taps there read 0
     const float2 lo = f2(-2.0f - e.o.x, -2.0f - e.o.y);
     const float2 hi = f2((float)(W + 1) - e.o.x, (float)(H + 1) - e.o.y);
+    // (u', v', w) stepped along the run as in the packed paths: one chain for
+    // the even voxels and one for the odd, two voxels per step
+    float w0 = fmaf((float)(-R / 2), e.w.w, vb.w), w1 = fmaf((float)(1 - R / 2), e.w.w, vb.w);
+    float2 q0 = __ffma2_rn(f2((float)(-R / 2)), gz, vb.uv), q1 = __ffma2_rn(f2((float)(1 - R / 2)), gz, vb.uv);
+    const float g2w = e.w.w + e.w.w;
+    const float2 g2 = __fadd2_rn(gz, gz);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const float rf = (float)(r - R / 2);
-        const float wl = fmaf(rf, e.w.w, vb.w);
+        if (r >= 2) {
+            if (r & 1) { w1 += g2w; q1 = __fadd2_rn(q1, g2); }
+            else { w0 += g2w; q0 = __fadd2_rn(q0, g2); }
+        }
+        const float wl = (r & 1) ? w1 : w0;
         const float iw = rcp_approx(wl);
-        float2 uv = __fmul2_rn(__ffma2_rn(f2(rf), gz, vb.uv), f2(iw));
+        float2 uv = __fmul2_rn((r & 1) ? q1 : q0, f2(iw));
         uv = f2(fminf(fmaxf(uv.x, lo.x), hi.x), fminf(fmaxf(uv.y, lo.y), hi.y));
         const float2 t = __fadd2_rd(uv, f2(kFloorMagic));
         const float2 fl = __fadd2_rn(t, f2(-kFloorMagic));

@@ -15,8 +15,8 @@ fdk_bp_stage_kernel(const __grid_constant__ BpArgs a)
     // the resident CTAs' footprints overlapping, so their boxes hit in L2
     const int tx = a.walk_y ? blockIdx.y : blockIdx.x, ty = a.walk_y ? blockIdx.x : blockIdx.y;
     stage_init(sb);
-    stage_tile<BX, BY, WX, R, FIDX>(a, a.tmap, a.err, a.wait_limit, tx * BX, ty * BY, blockIdx.z * R, t, sb,
-                                    stages);
+    stage_tile<BX, BY, WX, R, FIDX, kNumBoxH>(a, a.tmap, a.err, a.wait_limit, tx * BX, ty * BY, blockIdx.z * R,
+                                              t, sb, stages);
 }
 
 template <int WX, bool FIDX>

@@ -27,6 +27,7 @@ constexpr long long kWaitLimit = 1LL << 22;
 // pixels (32 KB); views whose box is larger keep the global-load path.
 constexpr int kNumBoxW = 7;
 constexpr int kBoxRows = 8;
+constexpr int kNumBoxH = 4;        // plain launches: boxes of 8, 16, 32 and 64 rows
 constexpr int kStageFloats = 8192;
 __host__ __device__ constexpr int box_width(int m) { return 32 + 16 * m; }
 
@@ -57,8 +58,9 @@ struct BpArgs {
     float mats[KMAX * 12];     // host matrices of this pass (when mats_dev == nullptr)
     union {
         unsigned long long tex[KMAX];  // texture objects (texture fetch path only)
-        CUtensorMap tmap[kNumBoxW];    // staged path: the pass's images as a W x H x n
-                                       // tensor, one map per box width, 8-row boxes
+        CUtensorMap tmap[kNumBoxW * kNumBoxH];  // staged path: the pass's images as a
+                                                // W x H x n tensor, one map per box width
+                                                // and height (8 << h rows), [m * kNumBoxH + h]
     };
     int vidx[KMAX];            // image index (within the pass's images) of each view
 };

@@ -12,16 +12,19 @@
 //
 // Pipeline per CTA: kStages shared-memory stages.  Every thread waits on the
 // stage's mbarrier and computes the view; after a CTA barrier (the stage is
-// then free) warp 0 issues the copy of the staged view kStages further on
-// into it, one 8-row box per lane, so the next view's copy is in flight
-// while the CTA computes.
+// then free) thread 0 issues the copy of the staged view kStages further on
+// into it, so the next view's copy is in flight while the CTA computes.  The
+// copy goes in as few TMA boxes as the map heights allow (8 to 64 rows on a
+// plain launch), because the issuing warp lags the next barrier by the
+// issue's length.
 // Each thread owns a z-run of 16 voxels, so the per-view barrier is shared
 // by 16 updates per thread (8 per thread measured 10% slower, 24 slower
 // still).  (A barrier-free variant, in which the last warp done with a stage
 // refills it, measured 12% slower: its warps spin on the mbarriers instead.)
-// Every wait is bounded; a wait that gives up sets *a.err, thread 0 drains
-// the copies still in flight (again bounded) and the CTA returns without
-// writing its tile.  The taps are read with 32-bit shared addresses.
+// Every wait is bounded; a thread whose wait gives up raises a shared flag
+// that all read after the barrier: *err is set, thread 0 drains the copies
+// still in flight (again bounded) and the CTA stops without writing its
+// tile.  The taps are read with 32-bit shared addresses.
 #pragma once
 
 #include "fdk_bp_kernel.cuh"
@@ -30,7 +33,6 @@ namespace fdk {
 
 constexpr int kStages = 2;
 constexpr int kStageChunk = 64;          // views per table chunk on this path
-
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -56,8 +58,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 }
 
 // Copy the box of table entry lv (view v0 + lv of the pass) into stage st.
-// Called by one thread.
-template <class A>
+// Called by one thread.  tmaps holds NH maps per box width, of boxes 8, 16,
+// .., 8 * 2^(NH-1) rows high: the box's rows8 8-row blocks go in as few copies
+// as those heights allow (one copy per set bit of rows8, tallest first).
+template <int NH, class A>
 __device__ __forceinline__ void stage_issue(const A &a, const CUtensorMap *tmaps, int v0, int lv,
                                             const int4 *sbox, float *stages, uint32_t full0, unsigned st)
 {
@@ -71,15 +75,21 @@ __device__ __forceinline__ void stage_issue(const A &a, const CUtensorMap *tmaps
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(bar), "r"(bytes) : "memory");
     const uint32_t dst = smem_addr(stages + (size_t)st * kStageFloats);
-    const CUtensorMap *map = tmaps + b.z;
     const int img = a.vidx[v0 + lv];
-    for (int r = 0; r < b.w; ++r) {
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];"
-            :: "r"(dst + (uint32_t)(r * kBoxRows * BW) * 4u), "l"(map), "r"(b.x),
-               "r"(b.y + r * kBoxRows), "r"(img), "r"(bar)
-            : "memory");
+    int r = 0, left = b.w;
+#pragma unroll
+    for (int h = NH - 1; h >= 0; --h) {
+        const CUtensorMap *map = tmaps + b.z * NH + h;
+        while (left >= (1 << h)) {
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];"
+                :: "r"(dst + (uint32_t)(r * kBoxRows * BW) * 4u), "l"(map), "r"(b.x),
+                   "r"(b.y + r * kBoxRows), "r"(img), "r"(bar)
+                : "memory");
+            r += 1 << h;
+            left -= 1 << h;
+        }
     }
 }
 
@@ -119,13 +129,21 @@ __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e,
     // magic folded into the bases
     const uint32_t sbase = smem_addr(stage) - (kIndexBits << 2);
     const uint32_t sbase1 = sbase + ((uint32_t)(int)e.o.w << 2);
+    // (u', v', w) of the run's first two voxels, then stepped two voxels at a
+    // time (the steps 2 g are exact)
+    const float2 RF0 = f2((float)(-R / 2), (float)(1 - R / 2));
+    float2 wl = __ffma2_rn(RF0, GW, BW), uq = __ffma2_rn(RF0, GU, BU), vq = __ffma2_rn(RF0, GV, BV);
+    const float2 G2W = __fadd2_rn(GW, GW), G2U = __fadd2_rn(GU, GU), G2V = __fadd2_rn(GV, GV);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
-        const float2 wl = __ffma2_rn(RF, GW, BW);
+        if (r > 0) {
+            wl = __fadd2_rn(wl, G2W);
+            uq = __fadd2_rn(uq, G2U);
+            vq = __fadd2_rn(vq, G2V);
+        }
         const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
-        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
-        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 u = __fmul2_rn(uq, iw);
+        const float2 v = __fmul2_rn(vq, iw);
         const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
         const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
@@ -158,6 +176,7 @@ struct StageBarriers {
     unsigned long long full[kStages];
     unsigned nissue[kStages];              // copies issued into each stage so far
     unsigned consumed;                     // staged views consumed so far (uniform)
+    unsigned failed;                       // set by a thread whose bounded wait gave up
 };
 
 // Called once per CTA by all threads before the first stage_tile.
@@ -170,6 +189,7 @@ __device__ __forceinline__ void stage_init(StageBarriers &sb)
             sb.nissue[s] = 0;
         }
         sb.consumed = 0;
+        sb.failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -182,7 +202,7 @@ __device__ __forceinline__ void stage_init(StageBarriers &sb)
 // this.  Returns false, with the tile unwritten, when a bounded wait gave up
 // (the CTA must then stop using the stages); *err is set and the copies in
 // flight are drained.
-template <int BX, int BY, int WX, int R, bool FIDX, class A>
+template <int BX, int BY, int WX, int R, bool FIDX, int NH, class A>
 __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps, unsigned *err, long long wait_limit,
                                            int x0, int y0, int z0, StageTables &t, StageBarriers &sb,
                                            float *stages)
@@ -227,7 +247,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
                 // the first copies of the chunk
                 for (int k = 0; k < kStages && k < count; ++k) {
                     const unsigned st = (base + k) % kStages;
-                    stage_issue(a, tmaps, v0, t.stg[k], t.sbox, stages, full0, st);
+                    stage_issue<NH>(a, tmaps, v0, t.stg[k], t.sbox, stages, full0, st);
                     ++sb.nissue[st];
                 }
             }
@@ -241,11 +261,12 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
             if (c == kStaged) {
                 const unsigned slot = base + kst;
                 const unsigned st = slot % kStages;
-                const bool ok = mbar_wait(full0 + 8u * st, (slot / kStages) & 1u, wait_limit);
+                if (!mbar_wait(full0 + 8u * st, (slot / kStages) & 1u, wait_limit)) sb.failed = 1u;
                 const ViewEntry e = t.tab[lv];
                 view_staged<R>(acc, e, dxf, dyf, stages + (size_t)st * kStageFloats);
                 ++kst;
-                if (!__syncthreads_and(ok)) {
+                __syncthreads();
+                if (sb.failed) {
                     if (tid == 0) {
                         atomicOr(err, 1u);
                         // drain with the full limit: no copy may still be
@@ -258,7 +279,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
                 if (tid == 0) {
                     const unsigned nk = kst - 1 + kStages;
                     if (nk < ns) {
-                        stage_issue(a, tmaps, v0, t.stg[nk], t.sbox, stages, full0, st);
+                        stage_issue<NH>(a, tmaps, v0, t.stg[nk], t.sbox, stages, full0, st);
                         ++sb.nissue[st];
                     }
                 }
