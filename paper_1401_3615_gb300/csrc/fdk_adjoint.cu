@@ -98,13 +98,22 @@ __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry
     const float2 SC = f2(scale);
     const uint32_t abase = (uint32_t)__cvta_generic_to_shared(acc_v) - (kIndexBits << 2);
     const uint32_t abase1 = abase + ((uint32_t)bb.z << 2);
+    // (u', v', w) of the run's first two voxels, then stepped two voxels at a
+    // time, exactly as the back-projection steps them (so the two operators
+    // see the same detector positions)
+    const float2 RF0 = f2((float)(-R / 2), (float)(1 - R / 2));
+    float2 wl = __ffma2_rn(RF0, GW, BWW), uq = __ffma2_rn(RF0, GU, BU), vq = __ffma2_rn(RF0, GV, BV);
+    const float2 G2W = __fadd2_rn(GW, GW), G2U = __fadd2_rn(GU, GU), G2V = __fadd2_rn(GV, GV);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-        const float2 RF = f2((float)(r - R / 2), (float)(r + 1 - R / 2));
-        const float2 wl = __ffma2_rn(RF, GW, BWW);
+        if (r > 0) {
+            wl = __fadd2_rn(wl, G2W);
+            uq = __fadd2_rn(uq, G2U);
+            vq = __fadd2_rn(vq, G2V);
+        }
         const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
-        const float2 u = __fmul2_rn(__ffma2_rn(RF, GU, BU), iw);
-        const float2 v = __fmul2_rn(__ffma2_rn(RF, GV, BV), iw);
+        const float2 u = __fmul2_rn(uq, iw);
+        const float2 v = __fmul2_rn(vq, iw);
         const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
         const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
@@ -257,12 +266,21 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
             } else {
                 const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
                 const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
+                // stepped as in the back-projection: a chain for the even
+                // voxels of the run and one for the odd, two voxels per step
+                float w0 = fmaf((float)(-R / 2), e.w.w, bw), w1 = fmaf((float)(1 - R / 2), e.w.w, bw);
+                float2 q0 = __ffma2_rn(f2((float)(-R / 2)), gz, buv), q1 = __ffma2_rn(f2((float)(1 - R / 2)), gz, buv);
+                const float g2w = e.w.w + e.w.w;
+                const float2 g2 = __fadd2_rn(gz, gz);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float rf = (float)(r - R / 2);
-                    const float wl = fmaf(rf, e.w.w, bw);
+                    if (r >= 2) {
+                        if (r & 1) { w1 += g2w; q1 = __fadd2_rn(q1, g2); }
+                        else { w0 += g2w; q0 = __fadd2_rn(q0, g2); }
+                    }
+                    const float wl = (r & 1) ? w1 : w0;
                     const float iw = rcp_approx(wl);
-                    float2 uv = __fmul2_rn(__ffma2_rn(f2(rf), gz, buv), f2(iw));
+                    float2 uv = __fmul2_rn((r & 1) ? q1 : q0, f2(iw));
                     uv = f2(fminf(fmaxf(uv.x, lou), hiu), fminf(fmaxf(uv.y, lov), hiv));
                     const float2 t = __fadd2_rd(uv, f2(kFloorMagic));
                     const float au = uv.x - (t.x - kFloorMagic), bv = uv.y - (t.y - kFloorMagic);
