@@ -62,6 +62,12 @@ __device__ __forceinline__ void red_shared_pair(uint32_t addr, int v0, int v1)
     asm volatile("red.shared.add.s32 [%0+4], %1;" :: "r"(addr), "r"(v1) : "memory");
 }
 
+// One predicated shared-memory integer reduction.
+__device__ __forceinline__ void red_shared_if(bool p, uint32_t addr, int v)
+{
+    if (p) asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(addr), "r"(v) : "memory");
+}
+
 // The four weighted taps of a voxel: value g = f / w^2 and fractions (a, b).
 struct Taps {
     float w00, w10, w01, w11;
@@ -77,15 +83,19 @@ __device__ __forceinline__ Taps tap_weights(float g, float a, float b)
     return t;
 }
 
-// Fixed-point splat of one view for an interior tile: every tap lies in
-// the image and, by the 1-pixel margin of the footprint box bb, inside bb;
-// the clamp of the cell index only guards memory.  Each f32x2 pair holds one
+// Fixed-point splat of one view for an interior or boundary tile.  Interior:
+// every tap lies in the image and, by the 1-pixel margin of the footprint box
+// bb, inside bb; the clamp of the cell index only guards memory.  Each f32x2 pair holds one
 // quantity of two z neighbours, as in the forward's hot loop.  The
 // contribution f / w^2 is scaled to fixed point before it is split into the
 // four tap weights, and the cell index (j - j0) * bw + (i - i0) is formed in
 // FP32 (exact: below 2^14 plus the 2^23 index magic), whose bits then address
 // the cell directly.
-template <int R>
+// CHECK (boundary tiles): taps outside the image are dropped.  The box is
+// clipped to the image and holds every tap inside it, so each reduction is
+// predicated on its pixel lying in the box, and its address is formed from
+// the integer cell index.
+template <int R, bool CHECK>
 __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry &e, float2 buv, float bw,
                                             int U, int V, const int4 &bb, int npx, float scale, int *acc_v)
 {
@@ -96,7 +106,8 @@ __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry
     const float2 OFF = f2((float)((V - bb.y) * bb.z + (U - bb.x)) + kIndexMagic);
     const float kmax = (float)(npx - bb.z - 2) + kIndexMagic;
     const float2 SC = f2(scale);
-    const uint32_t abase = (uint32_t)__cvta_generic_to_shared(acc_v) - (kIndexBits << 2);
+    const uint32_t cbase = (uint32_t)__cvta_generic_to_shared(acc_v);
+    const uint32_t abase = cbase - (kIndexBits << 2);
     const uint32_t abase1 = abase + ((uint32_t)bb.z << 2);
     // (u', v', w) of the run's first two voxels, then stepped two voxels at a
     // time, exactly as the back-projection steps them (so the two operators
@@ -114,20 +125,48 @@ __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry
         const float2 iw = f2(rcp_approx(wl.x), rcp_approx(wl.y));
         const float2 u = __fmul2_rn(uq, iw);
         const float2 v = __fmul2_rn(vq, iw);
-        const float2 flu = __fadd2_rn(__fadd2_rd(u, M), NM);
-        const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
+        const float2 tu = __fadd2_rd(u, M), tv = __fadd2_rd(v, M);
+        const float2 flu = __fadd2_rn(tu, NM);
+        const float2 flv = __fadd2_rn(tv, NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
         const float2 g = __fmul2_rn(__fmul2_rn(iw, iw), __fmul2_rn(f2(f[r], f[r + 1]), SC));
         const float2 gh = __fmul2_rn(g, bv), gl = __ffma2_rn(gh, NEG, g);
         const float2 w10 = __fmul2_rn(gl, au), w00 = __ffma2_rn(w10, NEG, gl);
         const float2 w11 = __fmul2_rn(gh, au), w01 = __ffma2_rn(w11, NEG, gh);
-        float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OFF);
-        k = f2(fminf(fmaxf(k.x, kIndexMagic), kmax), fminf(fmaxf(k.y, kIndexMagic), kmax));
-        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
-        red_shared_pair(abase + o0, __float2int_rn(w00.x), __float2int_rn(w10.x));
-        red_shared_pair(abase1 + o0, __float2int_rn(w01.x), __float2int_rn(w11.x));
-        red_shared_pair(abase + o1, __float2int_rn(w00.y), __float2int_rn(w10.y));
-        red_shared_pair(abase1 + o1, __float2int_rn(w01.y), __float2int_rn(w11.y));
+        if (!CHECK) {
+            float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OFF);
+            k = f2(fminf(fmaxf(k.x, kIndexMagic), kmax), fminf(fmaxf(k.y, kIndexMagic), kmax));
+            const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
+            red_shared_pair(abase + o0, __float2int_rn(w00.x), __float2int_rn(w10.x));
+            red_shared_pair(abase1 + o0, __float2int_rn(w01.x), __float2int_rn(w11.x));
+            red_shared_pair(abase + o1, __float2int_rn(w00.y), __float2int_rn(w10.y));
+            red_shared_pair(abase1 + o1, __float2int_rn(w01.y), __float2int_rn(w11.y));
+        } else {
+            // box-relative pixel indices from the floor bits; the box is
+            // clipped to the image and holds every tap inside it, so a tap
+            // is kept exactly when it lies in the box (which also keeps
+            // every access in the buffer)
+            const int i0 = __float_as_int(tu.x) - kFloorBits + U - bb.x, j0 = __float_as_int(tv.x) - kFloorBits + V - bb.y;
+            const int i1 = __float_as_int(tu.y) - kFloorBits + U - bb.x, j1 = __float_as_int(tv.y) - kFloorBits + V - bb.y;
+            const unsigned bzu = (unsigned)bb.z, bwu = (unsigned)bb.w;
+            const bool a0 = (unsigned)i0 < bzu, a1 = (unsigned)(i0 + 1) < bzu;
+            const bool b0 = (unsigned)j0 < bwu, b1 = (unsigned)(j0 + 1) < bwu;
+            const bool c0 = (unsigned)i1 < bzu, c1 = (unsigned)(i1 + 1) < bzu;
+            const bool d0 = (unsigned)j1 < bwu, d1 = (unsigned)(j1 + 1) < bwu;
+            // cell addresses in integers: a voxel one cell above or left of
+            // the box still has taps inside it, at a negative base index
+            const uint32_t q0 = cbase + (uint32_t)(j0 * bb.z + i0) * 4u;
+            const uint32_t q1 = cbase + (uint32_t)(j1 * bb.z + i1) * 4u;
+            const uint32_t rowb = (uint32_t)bb.z * 4u;
+            red_shared_if(a0 && b0, q0, __float2int_rn(w00.x));
+            red_shared_if(a1 && b0, q0 + 4u, __float2int_rn(w10.x));
+            red_shared_if(a0 && b1, q0 + rowb, __float2int_rn(w01.x));
+            red_shared_if(a1 && b1, q0 + rowb + 4u, __float2int_rn(w11.x));
+            red_shared_if(c0 && d0, q1, __float2int_rn(w00.y));
+            red_shared_if(c1 && d0, q1 + 4u, __float2int_rn(w10.y));
+            red_shared_if(c0 && d1, q1 + rowb, __float2int_rn(w01.y));
+            red_shared_if(c1 && d1, q1 + rowb + 4u, __float2int_rn(w11.y));
+        }
     }
 }
 
@@ -262,7 +301,9 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                     adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
                 }
             } else if (fixed && c == kInterior) {
-                splat_fixed<R>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
+                splat_fixed<R, false>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
+            } else if (fixed && c == kBoundary) {
+                splat_fixed<R, true>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
             } else {
                 const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
                 const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
