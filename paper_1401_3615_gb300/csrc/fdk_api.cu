@@ -401,9 +401,11 @@ static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
 }
 
 // Adjoint warp patches (voxels along x) for views whose rays run mostly along
-// x (4 x 8: 8 across the rays) and along y (8 x 4).  Measured against 2 x 16 /
-// 16 x 2 (same) and 8 x 4 for every view (3% slower at 512^3 x 496).
-constexpr int kAdjPatchAlongX = 4, kAdjPatchAlongY = 8;
+// x (2 x 16: 16 across the rays) and along y (16 x 2).  Lanes along a ray
+// mostly reduce into the same shared cell, and those reductions serialise;
+// 2 x 16 took 1.4% less than 4 x 8 at 512^3 x 496, and 8 x 4 for every view
+// 3% more.
+constexpr int kAdjPatchAlongX = 2, kAdjPatchAlongY = 16;
 
 // z-run of the adjoint's tiles for host matrices.  A 16-voxel run halves the
 // table builds and CTA barriers per voxel but doubles each tile's footprint,

@@ -53,8 +53,9 @@ constexpr unsigned kIndexBits = 0x4B000000u;
 // side against FP32 rounding; it may extend past the image, where the copy
 // reads zeros -- exactly the zero-outside rule of the interpolation.
 // With bbox != nullptr it also stores, per view, the pixel box that holds
-// every in-image tap of the tile, (i0, j0, width, height), widened by one
-// pixel against FP32 rounding and clipped to the image, and in wrange the
+// every in-image tap of the tile, (i0, j0, width, height), widened by 1/64
+// pixel against FP32 rounding (the per-voxel positions agree with the corners'
+// to about 1e-5 pixel) and clipped to the image, and in wrange the
 // smallest and largest w of the tile's corners (of the whole tile, since w
 // is linear in the voxel position).
 template <int BX, int BY, int R, class A, bool STAGE = false>
@@ -172,10 +173,10 @@ __device__ void build_view_table(const A &a, int v0, int nv, int x0, int y0, int
             int4 bb = make_int4(0, 0, 0, 0);
             if (c == kInterior || c == kBoundary) {
                 const float Hf = (float)g.H;
-                const int i0 = max(0, (int)floorf(fmaxf(umin, -4.0f)) - 1);
-                const int i1 = min(g.W - 1, (int)floorf(fminf(umax, Wf + 4.0f)) + 2);
-                const int j0 = max(0, (int)floorf(fmaxf(vmin, -4.0f)) - 1);
-                const int j1 = min(g.H - 1, (int)floorf(fminf(vmax, Hf + 4.0f)) + 2);
+                const int i0 = max(0, (int)floorf(fmaxf(umin - eps, -4.0f)));
+                const int i1 = min(g.W - 1, (int)floorf(fminf(umax + eps, Wf + 4.0f)) + 1);
+                const int j0 = max(0, (int)floorf(fmaxf(vmin - eps, -4.0f)));
+                const int j1 = min(g.H - 1, (int)floorf(fminf(vmax + eps, Hf + 4.0f)) + 1);
                 if (i1 >= i0 && j1 >= j0) bb = make_int4(i0, j0, i1 - i0 + 1, j1 - j0 + 1);
             }
             bbox[lv] = bb;
