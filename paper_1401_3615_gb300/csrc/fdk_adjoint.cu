@@ -97,14 +97,14 @@ __device__ __forceinline__ Taps tap_weights(float g, float a, float b)
 // the integer cell index.
 template <int R, bool CHECK>
 __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry &e, float2 buv, float bw,
-                                            int U, int V, const int4 &bb, int npx, float scale, int *acc_v)
+                                            const int4 &bb, const int4 &sp, float scale, int *acc_v)
 {
     const float2 BU = f2(buv.x), BV = f2(buv.y), BWW = f2(bw);
     const float2 GU = f2(e.b.z), GV = f2(e.b.w), GW = f2(e.w.w);
     const float2 M = f2(kFloorMagic), NM = f2(-kFloorMagic), NEG = f2(-1.0f);
     const float2 PITCH = f2((float)bb.z);
-    const float2 OFF = f2((float)((V - bb.y) * bb.z + (U - bb.x)) + kIndexMagic);
-    const float kmax = (float)(npx - bb.z - 2) + kIndexMagic;
+    const float2 OFF = f2(__int_as_float(sp.x));
+    const float kmax = __int_as_float(sp.y);
     const float2 SC = f2(scale);
     const uint32_t cbase = (uint32_t)__cvta_generic_to_shared(acc_v);
     const uint32_t abase = cbase - (kIndexBits << 2);
@@ -146,8 +146,8 @@ __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry
             // clipped to the image and holds every tap inside it, so a tap
             // is kept exactly when it lies in the box (which also keeps
             // every access in the buffer)
-            const int i0 = __float_as_int(tu.x) - kFloorBits + U - bb.x, j0 = __float_as_int(tv.x) - kFloorBits + V - bb.y;
-            const int i1 = __float_as_int(tu.y) - kFloorBits + U - bb.x, j1 = __float_as_int(tv.y) - kFloorBits + V - bb.y;
+            const int i0 = __float_as_int(tu.x) - kFloorBits + sp.z, j0 = __float_as_int(tv.x) - kFloorBits + sp.w;
+            const int i1 = __float_as_int(tu.y) - kFloorBits + sp.z, j1 = __float_as_int(tv.y) - kFloorBits + sp.w;
             const unsigned bzu = (unsigned)bb.z, bwu = (unsigned)bb.w;
             const bool a0 = (unsigned)i0 < bzu, a1 = (unsigned)(i0 + 1) < bzu;
             const bool b0 = (unsigned)j0 < bwu, b1 = (unsigned)(j0 + 1) < bwu;
@@ -182,7 +182,9 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     __shared__ unsigned char cls[kAdjChunk];
     __shared__ unsigned short act[kAdjChunk];
     __shared__ int4 bbox[kAdjChunk];
-    __shared__ float2 wrange[kAdjChunk];
+    __shared__ float2 wrange[kAdjChunk];   // w range of the tile, then (scale, 1 / scale)
+    __shared__ int4 vflags[kAdjChunk];     // (flags, row divisor, flush step, view index)
+    __shared__ int4 vsplat[kAdjChunk];     // (cell offset, last base cell, column, row offsets)
     __shared__ int n_act;
     extern __shared__ __align__(16) int acc_s[];   // kAdjCap cells: fixed point, or FP32 bits
     __shared__ float red_s[NT / 32];
@@ -230,11 +232,13 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
     for (int v0 = 0; v0 < a.n_views; v0 += kAdjChunk) {
         const int nv = min(kAdjChunk, a.n_views - v0);
         build_view_table<BX, BY, R>(a, v0, nv, x0, y0, z0, tab, cls, act, &n_act, bbox, wrange);
-        prev_lo = prev_hi = 0;     // the table build ends with a barrier
-        const int n = n_act;
-        for (int q = 0; q < n; ++q) {
-            const int ev = act[q];
-            const int lv = ev & 1023, c = ev >> 10;
+        // what every thread needs of a view but depends on the view alone,
+        // once per view: the box (widened to 4-cell groups for the vector
+        // flush), the fixed-point scale, whether FP64 positions are needed,
+        // and the flush's (row, group) stepping without a division
+        for (int lv = tid; lv < nv; lv += NT) {
+            const int c = cls[lv];
+            if (c == kSkip) continue;
             const ViewEntry e = tab[lv];
             int4 bb = bbox[lv];
             if (VEC4 && bb.z > 0) {
@@ -247,8 +251,40 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
             const bool fits = npx > 0 && npx <= kAdjCap;
             // fixed point when w varies little over the tile, else FP32 cells
             const bool fixed = fits && wr.x > 0.0f && wr.y <= 1.5f * wr.x;
-            const float scale = fixed ? 2147475456.0f * (wr.x * wr.x) / ftile : 0.0f;
-            const float inv_scale = fixed ? ftile / (2147475456.0f * (wr.x * wr.x)) : 0.0f;
+            // FP32 rounding of the table's detector positions, about
+            // 2^-24 (|c| + extent |g|) / w pixels, bounded over the tile;
+            // the splat's tap weights move by that much
+            const float tu = fabsf(e.a.x) + (BX / 2) * fabsf(e.a.z) + (BY / 2) * fabsf(e.b.x) +
+                             (R / 2) * fabsf(e.b.z);
+            const float tv = fabsf(e.a.y) + (BX / 2) * fabsf(e.a.w) + (BY / 2) * fabsf(e.b.y) +
+                             (R / 2) * fabsf(e.b.w);
+            const bool precise = c == kGeneral || !(wr.x > 0.0f) ||
+                                 fmaxf(tu, tv) * 5.9604645e-8f > kPreciseUV * wr.x;
+            const float sc = fixed ? 2147475456.0f * (wr.x * wr.x) / ftile : 0.0f;
+            const int gw = VEC4 ? bb.z >> 2 : bb.z;   // flush items per row
+            const int rowdiv = gw > 0 ? (16777216 + gw - 1) / gw : 0;
+            const int drow = gw > 0 ? NT / gw : 0;
+            const int U = (int)e.o.x, V = (int)e.o.y;
+            bbox[lv] = bb;
+            wrange[lv] = make_float2(sc, fixed ? ftile / (2147475456.0f * (wr.x * wr.x)) : 0.0f);
+            vflags[lv] = make_int4((fits ? 1 : 0) | (fixed ? 2 : 0) | (precise ? 4 : 0), rowdiv,
+                                   drow | ((NT - drow * gw) << 16), a.vidx[v0 + lv]);
+            vsplat[lv] = make_int4(__float_as_int((float)((V - bb.y) * bb.z + (U - bb.x)) + kIndexMagic),
+                                   __float_as_int((float)(npx - bb.z - 2) + kIndexMagic), U - bb.x, V - bb.y);
+        }
+        __syncthreads();
+        prev_lo = prev_hi = 0;
+        const int n = n_act;
+        for (int q = 0; q < n; ++q) {
+            const int ev = act[q];
+            const int lv = ev & 1023, c = ev >> 10;
+            const ViewEntry e = tab[lv];
+            const int4 bb = bbox[lv];
+            const int4 vf = vflags[lv];
+            const int npx = bb.z * bb.w;
+            const bool fits = (vf.x & 1) != 0, fixed = (vf.x & 2) != 0, precise = (vf.x & 4) != 0;
+            const float2 sc = wrange[lv];
+            const float scale = sc.x, inv_scale = sc.y;
             int *acc_v = acc_s;
             if (fits) {
                 const int lo = (npx <= kAdjCap / 2 && prev_lo == 0 && prev_hi > 0) ? kAdjCap / 2 : 0;
@@ -257,20 +293,10 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                 prev_lo = lo;
                 prev_hi = lo + npx;
             }
-            float *proj = proj_out + (long long)a.vidx[v0 + lv] * a.plane;
+            float *proj = proj_out + (long long)vf.w * a.plane;
             const float2 buv = __ffma2_rn(f2(dyf), f2(e.b.x, e.b.y), __ffma2_rn(f2(dxf), f2(e.a.z, e.a.w), f2(e.a.x, e.a.y)));
             const float bw = fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x));
             const float2 gz = f2(e.b.z, e.b.w);
-            const int U = (int)e.o.x, V = (int)e.o.y;
-            // FP32 rounding of the table's detector positions, about
-            // 2^-24 (|c| + extent |g|) / w pixels, bounded over the tile
-            // (uniform); the splat's tap weights move by that much.
-            const float tu = fabsf(e.a.x) + (BX / 2) * fabsf(e.a.z) + (BY / 2) * fabsf(e.b.x) +
-                             (R / 2) * fabsf(e.b.z);
-            const float tv = fabsf(e.a.y) + (BX / 2) * fabsf(e.a.w) + (BY / 2) * fabsf(e.b.y) +
-                             (R / 2) * fabsf(e.b.w);
-            const bool precise = c == kGeneral || !(wr.x > 0.0f) ||
-                                 fmaxf(tu, tv) * 5.9604645e-8f > kPreciseUV * wr.x;
             if (precise) {
                 // close to the source (or across its plane): each voxel's
                 // (u', v', w) from the matrix in FP64 and u = u'/w, v = v'/w
@@ -301,10 +327,11 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                     adj_tap_checked(acc_v, fixed, scale, proj, bb, fits, W, H, i + 1, j + 1, k.w11);
                 }
             } else if (fixed && c == kInterior) {
-                splat_fixed<R, false>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
+                splat_fixed<R, false>(f, e, buv, bw, bb, vsplat[lv], scale, acc_v);
             } else if (fixed && c == kBoundary) {
-                splat_fixed<R, true>(f, e, buv, bw, U, V, bb, npx, scale, acc_v);
+                splat_fixed<R, true>(f, e, buv, bw, bb, vsplat[lv], scale, acc_v);
             } else {
+                const int U = (int)e.o.x, V = (int)e.o.y;
                 const float lou = -2.0f - e.o.x, lov = -2.0f - e.o.y;
                 const float hiu = (float)(W + 1) - e.o.x, hiv = (float)(H + 1) - e.o.y;
                 // stepped as in the back-projection: a chain for the even
@@ -342,9 +369,9 @@ fdk_adj_kernel(const __grid_constant__ BpArgs a, float *__restrict__ proj_out)
                 if (VEC4) {
                     const int gw = bb.z >> 2;
                     int4 *acc4 = reinterpret_cast<int4 *>(acc_v);
-                    // (row, group) of p, stepped along with p (one division per view)
-                    int row = tid / gw, grp = tid - row * gw;
-                    const int drow = NT / gw, dgrp = NT - drow * gw;
+                    // (row, group) of p, stepped along with p
+                    int row = (int)(((unsigned)tid * (unsigned)vf.y) >> 24), grp = tid - row * gw;
+                    const int drow = vf.z & 0xFFFF, dgrp = vf.z >> 16;
                     for (int p = tid; p < (npx >> 2); p += NT) {
                         const int4 s4 = acc4[p];
                         const int col = grp << 2, rw = row;
