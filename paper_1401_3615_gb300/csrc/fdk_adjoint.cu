@@ -62,10 +62,27 @@ __device__ __forceinline__ void red_shared_pair(uint32_t addr, int v0, int v1)
     asm volatile("red.shared.add.s32 [%0+4], %1;" :: "r"(addr), "r"(v1) : "memory");
 }
 
-// One predicated shared-memory integer reduction.
-__device__ __forceinline__ void red_shared_if(bool p, uint32_t addr, int v)
+// The four taps of one voxel of a boundary tile: cells (i, j), (i + 1, j) at
+// shared address q0 and the next, (i, j + 1), (i + 1, j + 1) at q1 and the
+// next, each reduced only when it lies in the box of bz x bh cells (i, j
+// box-relative).  The tests are predicates of the reductions, not branches.
+__device__ __forceinline__ void red_shared_quad_in_box(uint32_t q0, uint32_t q1, int i, int j, unsigned bz,
+                                                       unsigned bh, int v00, int v10, int v01, int v11)
 {
-    if (p) asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(addr), "r"(v) : "memory");
+    asm volatile("{\n\t.reg .pred b0, b1, p;\n\t"
+                 "setp.lt.u32 b0, %2, %5;\n\t"
+                 "setp.lt.u32 b1, %3, %5;\n\t"
+                 "setp.lt.and.u32 p, %4, %6, b0;\n\t"
+                 "@p red.shared.add.s32 [%0], %8;\n\t"
+                 "setp.lt.and.u32 p, %7, %6, b0;\n\t"
+                 "@p red.shared.add.s32 [%0+4], %9;\n\t"
+                 "setp.lt.and.u32 p, %4, %6, b1;\n\t"
+                 "@p red.shared.add.s32 [%1], %10;\n\t"
+                 "setp.lt.and.u32 p, %7, %6, b1;\n\t"
+                 "@p red.shared.add.s32 [%1+4], %11;\n\t}"
+                 :: "r"(q0), "r"(q1), "r"(j), "r"(j + 1), "r"(i), "r"(bh), "r"(bz), "r"(i + 1),
+                    "r"(v00), "r"(v10), "r"(v01), "r"(v11)
+                 : "memory");
 }
 
 // The four weighted taps of a voxel: value g = f / w^2 and fractions (a, b).
@@ -149,23 +166,15 @@ __device__ __forceinline__ void splat_fixed(const float (&f)[R], const ViewEntry
             const int i0 = __float_as_int(tu.x) - kFloorBits + sp.z, j0 = __float_as_int(tv.x) - kFloorBits + sp.w;
             const int i1 = __float_as_int(tu.y) - kFloorBits + sp.z, j1 = __float_as_int(tv.y) - kFloorBits + sp.w;
             const unsigned bzu = (unsigned)bb.z, bwu = (unsigned)bb.w;
-            const bool a0 = (unsigned)i0 < bzu, a1 = (unsigned)(i0 + 1) < bzu;
-            const bool b0 = (unsigned)j0 < bwu, b1 = (unsigned)(j0 + 1) < bwu;
-            const bool c0 = (unsigned)i1 < bzu, c1 = (unsigned)(i1 + 1) < bzu;
-            const bool d0 = (unsigned)j1 < bwu, d1 = (unsigned)(j1 + 1) < bwu;
             // cell addresses in integers: a voxel one cell above or left of
             // the box still has taps inside it, at a negative base index
             const uint32_t q0 = cbase + (uint32_t)(j0 * bb.z + i0) * 4u;
             const uint32_t q1 = cbase + (uint32_t)(j1 * bb.z + i1) * 4u;
             const uint32_t rowb = (uint32_t)bb.z * 4u;
-            red_shared_if(a0 && b0, q0, __float2int_rn(w00.x));
-            red_shared_if(a1 && b0, q0 + 4u, __float2int_rn(w10.x));
-            red_shared_if(a0 && b1, q0 + rowb, __float2int_rn(w01.x));
-            red_shared_if(a1 && b1, q0 + rowb + 4u, __float2int_rn(w11.x));
-            red_shared_if(c0 && d0, q1, __float2int_rn(w00.y));
-            red_shared_if(c1 && d0, q1 + 4u, __float2int_rn(w10.y));
-            red_shared_if(c0 && d1, q1 + rowb, __float2int_rn(w01.y));
-            red_shared_if(c1 && d1, q1 + rowb + 4u, __float2int_rn(w11.y));
+            red_shared_quad_in_box(q0, q0 + rowb, i0, j0, bzu, bwu, __float2int_rn(w00.x), __float2int_rn(w10.x),
+                                   __float2int_rn(w01.x), __float2int_rn(w11.x));
+            red_shared_quad_in_box(q1, q1 + rowb, i1, j1, bzu, bwu, __float2int_rn(w00.y), __float2int_rn(w10.y),
+                                   __float2int_rn(w01.y), __float2int_rn(w11.y));
         }
     }
 }
