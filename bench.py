@@ -398,7 +398,9 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     h_proj = torch.empty(proj.shape, dtype=proj.dtype, pin_memory=True)
     h_proj.copy_(proj)
     h_vol = torch.zeros(vol.shape, dtype=vol.dtype, pin_memory=True)
-    e2e_steps = max(1, min(args.steps, 20))
+    # at least 20 steps: the host link has periodic slow phases (about every
+    # 0.5 s), and the mean should not hinge on whether one falls in a short run
+    e2e_steps = min(max(args.steps, 20), 40)
 
     def e2e_step():
         fdk.fdk_backproject_host(h_vol, h_proj, mats, vs, org, fetch=args.fetch, tile=args.tile,
@@ -435,7 +437,7 @@ def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):
     del dst
     return {"value": _job_rate(world, upd_full, e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": int(proj.numel() * proj.element_size()),
-            "d2h_bytes_per_step": vol_bytes, "ms_per_step": e2e_s * 1e3,
+            "d2h_bytes_per_step": vol_bytes, "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
             "ms_per_step_median": float(np.median(step_ms)), "step_ms": [round(t, 2) for t in step_ms],
             "plain_h2d_copy_ms": {"median": float(np.median(copy_ms)), "max": float(max(copy_ms)),
                                   "each": [round(t, 2) for t in copy_ms],
