@@ -298,7 +298,8 @@ typedef struct fdk_batch_plan_t *fdk_batch_plan;
 
 /*
  * fdk_batch_plan_create -- prepare the back-projection of n_scans scans of
- * uneven volume, view and detector size as one persistent launch.  Each
+ * uneven volume, view and detector size as one persistent launch (plus the
+ * own launches of scans that fill the GPU alone, below).  Each
  * scan is exactly one fdk_backproject call (Listing 1, Sec. IV); the batch
  * only changes how the work is scheduled.  The plan copies the scans'
  * descriptors, matrices and a (scan, tile) work list to device memory it
@@ -314,13 +315,21 @@ typedef struct fdk_batch_plan_t *fdk_batch_plan;
  * multiple of 4, a 16-byte aligned base, footprints that fit the stages),
  * on its own 16 x 16 x 16 tiles, for up to 32 scans of the batch, provided
  * the plan's tile variant has 16 x 16 threads (0, 5, 7); the other scans
- * take the global-load path on the plan's tile variant.  The autotuner times
- * the plan with and without staging those scans (one persistent kernel runs
- * both paths, at the staged path's 3 CTAs per SM, which can cost the
- * global-load scans more than staging saves) and keeps the faster.  FDK_FETCH_LDG: every scan takes the global-load
- * path.  fdk_batch_plan_scan_fetch tells which path a scan takes.  A staged
- * scan's bounded waits are reported by fdk_device_status(), as for
- * fdk_backproject.
+ * take the global-load path on the plan's tile variant.  A scan with at
+ * least two waves of the staged kernel's 16 x 16 x 16 tiles on its own
+ * (2 x 3 CTAs per SM) runs alone instead: its own launches, exactly those of
+ * fdk_backproject, prepared at plan creation and issued after the persistent
+ * kernel -- with FDK_FETCH_STAGE where the staged path applies as above (no
+ * limit on their number), else with FDK_FETCH_LDG and the plan's tile
+ * variant.  The autotuner
+ * times the plan with and without those scans running alone, and with and
+ * without staging the other stageable scans inside the persistent kernel
+ * (which then runs both paths at the staged path's 3 CTAs per SM, which can
+ * cost the global-load scans more than staging saves), and keeps the
+ * fastest.  FDK_FETCH_LDG: every scan takes the global-load path inside the
+ * persistent kernel.  fdk_batch_plan_scan_fetch tells which path a scan
+ * takes.  A staged scan's bounded waits are reported by fdk_device_status(),
+ * as for fdk_backproject.
  */
 FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans,
                                          int32_t n_scans, const fdk_opts *opts);
@@ -329,9 +338,10 @@ FDK_API fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *s
  * fdk_batch_plan_execute -- enqueue the batch on `stream` (cudaStream_t,
  * NULL = legacy default stream): a reset of the plan's work counter and one
  * persistent kernel in which CTAs take (scan, tile) items from that counter
- * until none are left.  Every volume is accumulated (+=) exactly as by
- * fdk_backproject, bit for bit: with FDK_FETCH_STAGE for the staged scans,
- * with FDK_FETCH_LDG and the plan's tile variant for the others.  It allocates nothing and does not synchronise.  Executions of one plan must not
+ * until none are left, then the launches of the scans that run alone.  Every
+ * volume is accumulated (+=) exactly as by fdk_backproject, bit for bit: with
+ * FDK_FETCH_STAGE for the staged scans (inside the kernel or alone), with
+ * FDK_FETCH_LDG and the plan's tile variant for the others.  It allocates nothing and does not synchronise.  Executions of one plan must not
  * overlap on the GPU (they share the counter); the plan's device must be
  * current.
  */

@@ -400,6 +400,27 @@ static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
     return encode_stage_maps_at(a.tmap, a.proj, W, H, nv, kNumBoxH);
 }
 
+// Host matrices: the views of pass [v0, v0 + nv) whose rays run mostly along
+// x (group 0) or along y (group 1) into a's matrices and view indices, with
+// the warp patch that touches the fewest L1 banks for them (4 x 8 along x,
+// 8 x 4 along y) and, on the staged path, CTAs walking along y for group 1.
+// Returns the views taken.
+static int fill_orientation_group(BpArgs &a, const float *matrices, int v0, int nv, int group, bool staged)
+{
+    int cnt = 0;
+    for (int k = 0; k < nv; ++k) {
+        const float *P = matrices + (size_t)(v0 + k) * 12;
+        const bool along_x = fabsf(P[8]) > fabsf(P[9]);
+        if (along_x != (group == 0)) continue;
+        memcpy(a.mats + 12 * cnt, P, sizeof(float) * 12);
+        a.vidx[cnt++] = k;
+    }
+    a.n_views = cnt;
+    a.warp_x = group == 0 ? 4 : 8;
+    a.walk_y = group == 1 && staged;
+    return cnt;
+}
+
 // Adjoint warp patches (voxels along x) for views whose rays run mostly along
 // x (2 x 16: 16 across the rays) and along y (16 x 2).  Lanes along a ray
 // mostly reduce into the same shared cell, and those reductions serialise;
@@ -812,18 +833,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         // along x: 4 x 8; along y: 8 x 4); each voxel still sums every view
         a.mats_dev = nullptr;
         for (int group = 0; group < 2; ++group) {
-            int cnt = 0;
-            for (int k = 0; k < nv; ++k) {
-                const float *P = matrices + (size_t)(v0 + k) * 12;
-                const bool along_x = fabsf(P[8]) > fabsf(P[9]);
-                if (along_x != (group == 0)) continue;
-                memcpy(a.mats + 12 * cnt, P, sizeof(float) * 12);
-                a.vidx[cnt++] = k;
-            }
-            if (cnt == 0) continue;
-            a.n_views = cnt;
-            a.warp_x = group == 0 ? 4 : 8;
-            a.walk_y = group == 1 && use_stage;
+            if (fill_orientation_group(a, matrices, v0, nv, group, use_stage) == 0) continue;
             if ((st = launch_backproject(a, fetch, o->proj_dtype, o->tile, s))) return st;
         }
     }
@@ -1314,6 +1324,14 @@ struct fdk_batch_plan_t {
     std::unique_ptr<fdk::BatchLaunch> launch;   // kernel arguments, staged scans' tensor maps included
     std::vector<int> stage_slot;     // per scan: its tensor maps' slot if it can be staged, else -1
     int n_stageable = 0;
+    // Scans that fill the GPU on their own may run as their own launches
+    // (exactly fdk_backproject's) instead of inside the persistent kernel:
+    // staged where the staged path applies, else on the global-load path with
+    // the plan's tile variant.
+    std::vector<char> alone_ok;      // per scan: may run alone
+    std::vector<char> alone;         // per scan: runs alone in this plan
+    std::vector<char> alone_staged;  // per scan: its own launches are staged
+    std::vector<std::pair<int, std::unique_ptr<fdk::BpArgs>>> alone_args;   // (scan, one launch's arguments)
 };
 
 namespace fdk {
@@ -1328,7 +1346,7 @@ static int plan_tile_start(const fdk_batch_plan_t *p, int tile, std::vector<int>
     for (int s = 0; s < p->n_scans; ++s) {
         ts[s] = (int)acc;
         const Geom &g = p->h_descs[2 * s].g;
-        const bool any = p->h_descs[2 * s].n_views + p->h_descs[2 * s + 1].n_views > 0;
+        const bool any = !p->alone[s] && p->h_descs[2 * s].n_views + p->h_descs[2 * s + 1].n_views > 0;
         // staged scans are cut into the staged path's tiles
         const bool staged = p->h_descs[2 * s].tmap_slot >= 0;
         const int sx = staged ? kStageTileXY : bx, sy = staged ? kStageTileXY : by, sz = staged ? kStageTileZ : r;
@@ -1352,16 +1370,32 @@ static fdk_status plan_set_tile(fdk_batch_plan_t *p, int tile)
     return FDK_OK;
 }
 
-static fdk_status plan_launch(fdk_batch_plan_t *p, cudaStream_t s)
+// The persistent kernel over the plan's work list, then the launches of the
+// scans that run alone (into vol_override instead of their volumes when it
+// is given, for the autotuner).
+static fdk_status plan_launch(fdk_batch_plan_t *p, cudaStream_t s, float *vol_override = nullptr)
 {
-    if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(FDK_ERR_CUDA, "batch: counter reset failed");
+    fdk_status st = FDK_OK;
+    if (p->total > 0) {
+        if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FDK_ERR_CUDA, "batch: counter reset failed");
+        }
+        BatchLaunch &b = *p->launch;
+        b.total = p->total;
+        b.wait_limit = consumer_wait_limit();
+        if ((st = launch_batched(b, p->tile, p->fidx, s))) return st;
     }
-    BatchLaunch &b = *p->launch;
-    b.total = p->total;
-    b.wait_limit = consumer_wait_limit();
-    return launch_batched(b, p->tile, p->fidx, s);
+    for (auto &al : p->alone_args) {
+        if (!p->alone[al.first]) continue;
+        BpArgs &a = *al.second;
+        a.vol = vol_override ? vol_override : p->h_descs[2 * (size_t)al.first].vol;
+        a.wait_limit = consumer_wait_limit();
+        const bool staged = p->alone_staged[al.first] != 0;
+        if ((st = launch_backproject(a, staged ? FDK_FETCH_STAGE : FDK_FETCH_LDG, FDK_F32, staged ? 0 : p->tile, s)))
+            return st;
+    }
+    return FDK_OK;
 }
 
 // Tile variants whose CTAs are 16 x 16 threads, as the staged scans' are:
@@ -1373,18 +1407,25 @@ static bool tile_is_16x16(int tile)
     return bx == kStageTileXY && by == kStageTileXY;
 }
 
-// Stage the scans that can be staged (on) or none of them (off).  The caller
-// uploads the descriptors.
+// Stage, inside the persistent kernel, the scans that can be staged and do
+// not run alone (on), or none of them (off).  The caller uploads the
+// descriptors.
 static void plan_set_staging(fdk_batch_plan_t *p, bool on)
 {
-    for (int s = 0; s < p->n_scans; ++s)
-        p->h_descs[2 * s].tmap_slot = p->h_descs[2 * s + 1].tmap_slot = on ? p->stage_slot[s] : -1;
-    p->launch->n_staged = on ? p->n_stageable : 0;
+    int n = 0;
+    for (int s = 0; s < p->n_scans; ++s) {
+        const int slot = (on && !p->alone[s]) ? p->stage_slot[s] : -1;
+        p->h_descs[2 * s].tmap_slot = p->h_descs[2 * s + 1].tmap_slot = slot;
+        n += slot >= 0;
+    }
+    p->launch->n_staged = n;
 }
 
-// Time the tile variants, with and without the staged path for the scans
-// that can take it, on the batch with every volume redirected to one scratch
-// buffer (the scans' volumes are never written); keep the fastest.
+// Time the tile variants, with and without the scans that may run alone
+// running alone, and with and without the staged path inside the kernel for
+// the other scans that can take it, on the batch with every volume
+// redirected to one scratch buffer (the scans' volumes are never written);
+// keep the fastest.
 static fdk_status plan_autotune(fdk_batch_plan_t *p)
 {
     size_t vmax = 0;
@@ -1402,31 +1443,38 @@ static fdk_status plan_autotune(fdk_batch_plan_t *p)
     cudaEventCreate(&e1);
     const int cands[] = {0, 2, 3, 4, 5, 7};
     int best = 0;
-    bool best_staged = false;
+    bool best_staged = false, best_alone = false;
     float best_ms = 3.0e38f;
     fdk_status st = FDK_OK;
-    for (int staged = 0; staged < 2 && st == FDK_OK; ++staged) {
-        if (staged && p->n_stageable == 0) break;
-        plan_set_staging(p, staged != 0);
-        std::vector<ScanDesc> tuned = p->h_descs;
-        for (auto &d : tuned) d.vol = scratch;
-        cudaMemcpy(p->d_descs, tuned.data(), sizeof(ScanDesc) * tuned.size(), cudaMemcpyHostToDevice);
-        for (int c : cands) {
-            if (staged && !tile_is_16x16(c)) continue;
-            if ((st = plan_set_tile(p, c))) break;
-            if ((st = plan_launch(p, 0))) break;            // warm-up
-            cudaEventRecord(e0, 0);
-            for (int rep = 0; rep < 2 && st == FDK_OK; ++rep) st = plan_launch(p, 0);
-            cudaEventRecord(e1, 0);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = fail(FDK_ERR_CUDA, "autotune: timing failed"); }
-            if (st) break;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) { best_ms = ms; best = c; best_staged = staged != 0; }
+    bool any_alone = false;
+    for (int s = 0; s < p->n_scans; ++s) any_alone |= p->alone_ok[s] != 0;
+    for (int alone = 0; alone < 2 && st == FDK_OK; ++alone) {
+        if (alone && !any_alone) break;
+        for (int s = 0; s < p->n_scans; ++s) p->alone[s] = alone ? p->alone_ok[s] : 0;
+        for (int staged = 0; staged < 2 && st == FDK_OK; ++staged) {
+            plan_set_staging(p, staged != 0);
+            if (staged && p->launch->n_staged == 0) break;
+            std::vector<ScanDesc> tuned = p->h_descs;
+            for (auto &d : tuned) d.vol = scratch;
+            cudaMemcpy(p->d_descs, tuned.data(), sizeof(ScanDesc) * tuned.size(), cudaMemcpyHostToDevice);
+            for (int c : cands) {
+                if (staged && !tile_is_16x16(c)) continue;
+                if ((st = plan_set_tile(p, c))) break;
+                if ((st = plan_launch(p, 0, scratch))) break;            // warm-up
+                cudaEventRecord(e0, 0);
+                for (int rep = 0; rep < 2 && st == FDK_OK; ++rep) st = plan_launch(p, 0, scratch);
+                cudaEventRecord(e1, 0);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); st = fail(FDK_ERR_CUDA, "autotune: timing failed"); }
+                if (st) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) { best_ms = ms; best = c; best_staged = staged != 0; best_alone = alone != 0; }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    for (int s = 0; s < p->n_scans; ++s) p->alone[s] = best_alone ? p->alone_ok[s] : 0;
     plan_set_staging(p, best_staged);
     cudaMemcpy(p->d_descs, p->h_descs.data(), sizeof(ScanDesc) * p->h_descs.size(), cudaMemcpyHostToDevice);
     cudaDeviceSynchronize();
@@ -1544,6 +1592,58 @@ fdk_status fdk_batch_plan_create(fdk_batch_plan *plan, const fdk_scan *scans, in
         }
         p->stage_slot[s] = slot;
     }
+    // Scans that cover two waves of the staged kernel's CTAs on their own run
+    // alone by default: their launches (per pass and ray orientation, as
+    // fdk_backproject builds them) are prepared here, so that an execution
+    // only launches.  Staged where fdk_backproject's AUTO would stage them.
+    p->alone_ok.assign(n_scans, 0);
+    p->alone.assign(n_scans, 0);
+    p->alone_staged.assign(n_scans, 0);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 0;
+    }
+    const long long alone_tiles = 2LL * 3 * (sms > 0 ? sms : 1);
+    unsigned *alone_err = nullptr;
+    for (int s = 0; s < n_scans; ++s) {
+        const fdk_scan &sc = scans[s];
+        const Geom &g = p->h_descs[2 * s].g;
+        const long long tiles = (long long)((g.nx + kStageTileXY - 1) / kStageTileXY) *
+                                ((g.ny + kStageTileXY - 1) / kStageTileXY) * ((g.nz + kStageTileZ - 1) / kStageTileZ);
+        if (sc.n_views < 1 || tiles < alone_tiles) continue;
+        const bool staged = o.fetch == FDK_FETCH_AUTO && tmap_encoder() && g.W % 4 == 0 &&
+                            ((uintptr_t)sc.projections) % 16 == 0 && stage_pays(g, sc.matrices, sc.n_views);
+        if (staged && !alone_err && (st = err_word(p->dev, &alone_err))) {
+            cudaFree(p->buf);
+            return st;
+        }
+        const long long plane = (long long)g.W * g.H;
+        for (int v0 = 0; v0 < sc.n_views; v0 += KMAX) {
+            const int nv = (sc.n_views - v0 < KMAX) ? (sc.n_views - v0) : KMAX;
+            for (int group = 0; group < 2; ++group) {
+                std::unique_ptr<BpArgs> a(new BpArgs());
+                a->g = g;
+                a->vol = sc.volume;
+                a->proj = static_cast<const float *>(sc.projections) + (size_t)v0 * plane;
+                a->plane = plane;
+                a->quads = nullptr;
+                a->qpitch = g.W + 3;
+                a->qplane = (long long)(g.W + 3) * (g.H + 3);
+                a->mats_dev = nullptr;
+                a->err = staged ? alone_err : nullptr;
+                if (staged && (st = encode_stage_maps(*a, g.W, g.H, nv))) {
+                    cudaFree(p->buf);
+                    return st;
+                }
+                if (fill_orientation_group(*a, sc.matrices, v0, nv, group, staged) == 0) continue;
+                p->alone_args.emplace_back(s, std::move(a));
+            }
+        }
+        p->alone_ok[s] = 1;
+        p->alone[s] = 1;
+        p->alone_staged[s] = staged;
+    }
     plan_set_staging(p.get(), true);
     L.descs = p->d_descs;
     L.tile_start = p->d_tile_start;
@@ -1594,7 +1694,8 @@ fdk_status fdk_batch_plan_scan_fetch(fdk_batch_plan plan, int32_t scan, int32_t 
     g_err[0] = 0;
     if (!plan || !fetch) return fail(FDK_ERR_INVALID_ARG, "null argument");
     if (scan < 0 || scan >= plan->n_scans) return fail(FDK_ERR_INVALID_ARG, "scan index out of range");
-    *fetch = plan->h_descs[2 * (size_t)scan].tmap_slot >= 0 ? FDK_FETCH_STAGE : FDK_FETCH_LDG;
+    const bool staged = plan->alone[scan] ? plan->alone_staged[scan] != 0 : plan->h_descs[2 * (size_t)scan].tmap_slot >= 0;
+    *fetch = staged ? FDK_FETCH_STAGE : FDK_FETCH_LDG;
     return FDK_OK;
 }
 

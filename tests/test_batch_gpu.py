@@ -106,6 +106,53 @@ def test_batch_with_fine_voxel_scans_staged():
     plan.close()
 
 
+def test_batch_with_a_scan_that_runs_alone():
+    """A scan at the 512^3 workload's pitch with two waves of the staged
+    kernel's tiles (192 x 192 x 128 voxels) runs as its own staged launches
+    after the persistent kernel: it, and the small scans in the kernel, equal
+    fdk_backproject bit for bit, also through CUDA-graph capture and replay;
+    the autotuner leaves the volumes alone and its pick matches too."""
+    cfg = synth.preset("fdk512", nx=192, ny=192, nz=128, n_views=24, seed=950)
+    s = synth.make_scan(cfg, device="cuda")
+    scans = [(torch.zeros((cfg.nz, cfg.ny, cfg.nx), device="cuda"), s["proj"], s["mats"],
+              s["voxel_size"], s["origin"])]
+    scans += _small_batch(n=4, seed=83)
+    plan = fdk.fdk_batch_plan_create(scans)
+    assert plan.scan_fetch(0) == fdk.FETCH_STAGE
+    ref = _sequential(scans, plan.tile, plan=plan)
+    plan.execute()
+    torch.cuda.synchronize()
+    fdk.fdk_device_status()
+    for (vol, *_), r in zip(scans, ref):
+        assert torch.equal(vol, r)
+    # graph capture records the kernel and the scan's own launches
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        plan.execute(stream=st)
+    for vol, *_ in scans:
+        vol.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    for (vol, *_), r in zip(scans, ref):
+        assert torch.equal(vol, r)
+    plan.close()
+    for vol, *_ in scans:
+        vol.fill_(1.5)
+    plan = fdk.fdk_batch_plan_create(scans, autotune=True)
+    torch.cuda.synchronize()
+    for vol, *_ in scans:
+        assert torch.all(vol == 1.5)
+    ref = _sequential(scans, plan.tile, init=1.5, plan=plan)
+    plan.execute()
+    torch.cuda.synchronize()
+    for (vol, *_), r in zip(scans, ref):
+        assert torch.equal(vol, r)
+    plan.close()
+
+
 def test_autotune_leaves_volumes_and_matches_its_tile():
     scans = _small_batch(seed=78)
     for vol, *_ in scans:
