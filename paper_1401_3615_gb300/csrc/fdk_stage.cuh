@@ -299,12 +299,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
     const int x = x0 + lx, y = y0 + ly;
     if (x < a.g.nx && y < a.g.ny) {
         const long long sxy = (long long)a.g.nx * a.g.ny;
-        float *col = a.vol + (long long)y * a.g.nx + x;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int z = z0 + r;
-            if (z < a.g.nz) col[z * sxy] += acc[r];
-        }
+        add_to_column<R>(a.vol + (long long)y * a.g.nx + x, sxy, z0, a.g.nz, acc);
     }
     return true;
 }

@@ -40,6 +40,19 @@ constexpr int kFloorBits = 0x4B400000;
 constexpr float kIndexMagic = 8388608.0f;
 constexpr unsigned kIndexBits = 0x4B000000u;
 
+// Add a thread's sums to its z-run of voxels (volume +=) with fire-and-forget
+// global reductions instead of a load, an add and a store: the load's latency
+// otherwise ends every tile (about 5 us per tile and launch at 512^3).  Each
+// voxel has one writer per launch, so the result is the plain
+// read-add-write's; the reduction flushes subnormal sums to zero.
+template <int R>
+__device__ __forceinline__ void add_to_column(float *col, long long sxy, int z0, int nz, const float (&acc)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (z0 + r < nz) atomicAdd(col + (long long)(z0 + r) * sxy, acc[r]);
+}
+
 // Fill tab[0..nv) for views v0..v0+nv of the pass and the compacted list
 // act[0..*n_act) of those whose class is not kSkip; act[q] = (v - v0) |
 // class << 10.  All threads of the CTA call this; it ends with
