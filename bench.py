@@ -380,10 +380,13 @@ def _preprocess_timing(args, world, dev, proj, mats, cfg):
 
 
 def _fft_len(W: int) -> int:
+    """The library's row FFT length: 2560 for rows of 1025..1280 pixels, else
+    the power of two >= 2W (at least 4)."""
     n = 1
     while n < 2 * W:
         n <<= 1
-    return max(n, 4)
+    n = max(n, 4)
+    return 2560 if n == 4096 and 2 * W <= 2560 else n
 
 
 def _e2e(args, world, dev, proj, vol, mats, vs, org, upd_full):

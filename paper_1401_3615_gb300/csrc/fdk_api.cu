@@ -1762,6 +1762,7 @@ extern "C" fdk_status fdk_preweight_filter(float *out, const float *in, const in
     int N = 1;
     while (N < 2 * det[0]) N <<= 1;
     if (N < 4) N = 4;
+    if (N == 4096 && 2 * det[0] <= 2560) N = 2560;   // 10 x 16 x 16: 60% of the work
     int dev = 0;
     cudaGetDevice(&dev);
     const float *spec = nullptr;

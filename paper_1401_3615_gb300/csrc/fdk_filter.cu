@@ -7,12 +7,13 @@
 //
 // with (f, u0, v0) read off view k's matrix through M M^T (square pixels, no
 // skew).  The linear convolution along a row is evaluated as a circular one
-// of length N = 2^ceil(log2(2W)) >= 2W (so every lag |m - m'| < W is within
-// N/2 and nothing wraps): two rows are packed as the real and imaginary
-// parts of one complex signal, transformed by a Stockham FFT, multiplied by
-// the kernel's spectrum (real, since h is even) and transformed back: for
-// N = 4096 three radix-16 passes with the points in registers, otherwise
-// radix-4 passes in shared memory.
+// of length N >= 2W (so every lag |m - m'| < W is within N/2 and nothing
+// wraps): N = 2560 for rows of 1025..1280 pixels, else 2^ceil(log2(2W)).
+// Two rows are packed as the real and imaginary parts of one complex signal,
+// transformed by a Stockham FFT, multiplied by the kernel's spectrum (real,
+// since h is even) and transformed back: for N = 2560 radix-10 and radix-16
+// passes, for N = 4096 three radix-16 passes, with the points in registers;
+// otherwise radix-4 passes in shared memory.
 #include <math.h>
 
 #include "fdk_internal.cuh"
@@ -45,7 +46,9 @@ __global__ void fdk_twiddle_kernel(float2 *tw, int N)
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     float sv, cv;
-    sincospif(2.0f * (float)t / (float)N, &sv, &cv);   // 2t/N is exact (N a power of two)
+    // 2t/N is exact for N a power of two, and rounded to half an ulp for
+    // N = 2560 (twiddles within about 2e-7)
+    sincospif(2.0f * (float)t / (float)N, &sv, &cv);
     tw[t] = make_float2(cv, -sv);
 }
 
@@ -302,10 +305,10 @@ __device__ __forceinline__ bool fmbar_wait(uint32_t bar, uint32_t parity, long l
     return false;
 }
 
-// Copy the rows of row pair rp into a stage (rows 2048 floats apart) with
+// Copy the rows of row pair rp into a stage (rows rowoff floats apart) with
 // bulk copies completing on the mbarrier at bar.  Called by one thread.
 __device__ __forceinline__ void filter_issue(const FilterArgs &a, long long rp, int pairs, float *stage,
-                                             uint32_t bar)
+                                             uint32_t bar, int rowoff = kF16N / 2)
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the stage's last reads
     const int k = (int)(rp / pairs), p = (int)(rp % pairs);
@@ -318,7 +321,7 @@ __device__ __forceinline__ void filter_issue(const FilterArgs &a, long long rp, 
                  :: "r"(fsmem(stage)), "l"(row1), "r"(rowbytes), "r"(bar) : "memory");
     if (r2 < a.H)
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(fsmem(stage + kF16N / 2)), "l"(row1 + a.W), "r"(rowbytes), "r"(bar) : "memory");
+                     :: "r"(fsmem(stage + rowoff)), "l"(row1 + a.W), "r"(rowbytes), "r"(bar) : "memory");
 }
 
 // STAGED: the rows (W % 4 == 0, 16-byte aligned) of the row pair after next
@@ -466,6 +469,276 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
     }
 }
 
+// N = 2560 (rows of 1025..1280 pixels, where the power-of-two length would
+// be 4096): 2560 = 10 x 16 x 16, about 60% of the 4096-point work.  Stockham
+// passes as in the 4096-point kernel -- the pass with radix R and stride Ns
+// has butterfly j read x[j + (N / R) m], scale it by w^m with
+// w = exp(-+2 pi i (j mod Ns) / (Ns R)), transform, and write output q to
+// (j - j mod Ns) R + j mod Ns + q Ns -- with radices 10, 16, 16 forward
+// (strides 1, 10, 160) and 16, 16, 10 inverse (strides 1, 16, 256).  The
+// radix-10 passes have 256 butterflies, one per thread; the radix-16 passes
+// 160, on the first five warps.  The last forward pass leaves thread j with
+// X[j + 160 q], the inputs of the first inverse pass, so the spectrum
+// multiply happens in registers; the last inverse pass leaves
+// result[j + 256 q].  The first exchange is unpadded (writes at stride 10:
+// two wavefronts per half-warp, reads conflict-free); the others are padded
+// one float2 per 16 (conflict-free both ways).
+constexpr int kF25N = 2560;
+
+// 5-point DFT, exp(-+2 pi i nk / 5).
+template <bool INV>
+__device__ __forceinline__ void dft5(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 &x4)
+{
+    // cos and sin of 2 pi / 5 and 4 pi / 5
+    constexpr float C1 = 0.30901699437494742f, C2 = -0.80901699437494742f;
+    constexpr float S1 = 0.95105651629515357f, S2 = 0.58778525229247313f;
+    const float2 t1 = cadd(x1, x4), t2 = cadd(x2, x3), t3 = csub(x1, x4), t4 = csub(x2, x3);
+    const float2 b1 = make_float2(x0.x + C1 * t1.x + C2 * t2.x, x0.y + C1 * t1.y + C2 * t2.y);
+    const float2 b2 = make_float2(x0.x + C2 * t1.x + C1 * t2.x, x0.y + C2 * t1.y + C1 * t2.y);
+    const float2 d1 = make_float2(S1 * t3.x + S2 * t4.x, S1 * t3.y + S2 * t4.y);
+    const float2 d2 = make_float2(S2 * t3.x - S1 * t4.x, S2 * t3.y - S1 * t4.y);
+    x0 = cadd(x0, cadd(t1, t2));
+    // forward: X1 = b1 - i d1, X4 = b1 + i d1, X2 = b2 - i d2, X3 = b2 + i d2
+    const float2 e1 = INV ? make_float2(-d1.y, d1.x) : make_float2(d1.y, -d1.x);   // -+ i d1
+    const float2 e2 = INV ? make_float2(-d2.y, d2.x) : make_float2(d2.y, -d2.x);
+    x1 = cadd(b1, e1);
+    x4 = csub(b1, e1);
+    x2 = cadd(b2, e2);
+    x3 = csub(b2, e2);
+}
+
+// 10-point DFT as 2 x 5: the pairs (x[n2], x[n2 + 5]), the twiddles
+// exp(-+2 pi i n2 k1 / 10), then 5-point DFTs over n2 giving X[k1 + 2 k2];
+// the result in natural order.
+template <bool INV>
+__device__ __forceinline__ void dft10(float2 (&x)[10])
+{
+    // cos and sin of pi j / 5, j = 1..4
+    constexpr float CA = 0.80901699437494742f, SA = 0.58778525229247313f;
+    constexpr float CB = 0.30901699437494742f, SB = 0.95105651629515357f;
+    const float sg = INV ? 1.0f : -1.0f;
+    float2 a[5], b[5];
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+        a[n] = cadd(x[n], x[n + 5]);
+        b[n] = csub(x[n], x[n + 5]);
+    }
+    b[1] = cmul(b[1], make_float2(CA, sg * SA));
+    b[2] = cmul(b[2], make_float2(CB, sg * SB));
+    b[3] = cmul(b[3], make_float2(-CB, sg * SB));
+    b[4] = cmul(b[4], make_float2(-CA, sg * SA));
+    dft5<INV>(a[0], a[1], a[2], a[3], a[4]);
+    dft5<INV>(b[0], b[1], b[2], b[3], b[4]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        x[2 * k] = a[k];
+        x[2 * k + 1] = b[k];
+    }
+}
+
+// Scale x[m] by w^m, w = tw[t1] (conjugated for the inverse), from the table
+// values w, w^2, w^4, w^8 and products, for m < R.
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_by(float2 (&x)[R], const float2 *__restrict__ tw, int t1)
+{
+    float2 w1 = __ldg(tw + t1), w2 = __ldg(tw + 2 * t1), w4 = __ldg(tw + 4 * t1), w8 = __ldg(tw + 8 * t1);
+    if (INV) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        w4.y = -w4.y;
+        w8.y = -w8.y;
+    }
+    const float2 w3 = cmul(w1, w2);
+    x[1] = cmul(x[1], w1);
+    x[2] = cmul(x[2], w2);
+    x[3] = cmul(x[3], w3);
+    x[4] = cmul(x[4], w4);
+    x[5] = cmul(x[5], cmul(w4, w1));
+    x[6] = cmul(x[6], cmul(w4, w2));
+    x[7] = cmul(x[7], cmul(w4, w3));
+    x[8] = cmul(x[8], w8);
+    x[9] = cmul(x[9], cmul(w8, w1));
+    if constexpr (R == 16) {
+        x[10] = cmul(x[10], cmul(w8, w2));
+        x[11] = cmul(x[11], cmul(w8, w3));
+        const float2 w12 = cmul(w8, w4);
+        x[12] = cmul(x[12], w12);
+        x[13] = cmul(x[13], cmul(w12, w1));
+        x[14] = cmul(x[14], cmul(w12, w2));
+        x[15] = cmul(x[15], cmul(w12, w3));
+    }
+}
+
+template <bool STAGED>
+__global__ void __launch_bounds__(256, 2)
+fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
+{
+    constexpr int N = kF25N, ROW = N / 2;
+    extern __shared__ __align__(128) float2 fsm[];
+    float2 *buf = fsm;                                             // N + N / 16 float2
+    float *stages = reinterpret_cast<float *>(fsm + N + N / 16);   // 2 x (2 rows of ROW)
+    __shared__ __align__(8) unsigned long long full[2];
+    const int j = threadIdx.x;
+    const bool b16 = j < N / 16;                  // the radix-16 passes' butterflies
+    const int pairs = (a.H + 1) / 2;
+    const long long total = (long long)pairs * a.n_views;
+    const long long stride = gridDim.x;
+    const uint32_t full0 = fsmem(full);
+    unsigned nis[2] = {0u, 0u};   // copies issued into each stage (thread 0)
+    if (STAGED) {
+        if (j == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full0) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full0 + 8u) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (j == 0) {
+            for (int q = 0; q < 2; ++q) {
+                const long long rq = blockIdx.x + q * stride;
+                if (rq < total) {
+                    filter_issue(a, rq, pairs, stages + q * N, full0 + 8u * q, ROW);
+                    ++nis[q];
+                }
+            }
+        }
+    }
+    int it = 0;
+    for (long long rp = blockIdx.x; rp < total; rp += stride, ++it) {
+        const int k = (int)(rp / pairs), p = (int)(rp % pairs);
+        const int r1 = 2 * p, r2 = 2 * p + 1;
+        // camera of view k from M M^T
+        float P[9];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                P[3 * q + c] = a.mats_dev ? __ldg(a.mats_dev + 12 * k + 4 * q + c) : a.mats[12 * k + 4 * q + c];
+        const float s2 = P[6] * P[6] + P[7] * P[7] + P[8] * P[8];
+        const float u0 = (P[0] * P[6] + P[1] * P[7] + P[2] * P[8]) / s2;
+        const float v0 = (P[3] * P[6] + P[4] * P[7] + P[5] * P[8]) / s2;
+        const float f2v = (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / s2 - u0 * u0;
+        const float f = sqrtf(f2v);
+        const float *row1, *row2;
+        const int st = it & 1;
+        bool ok = true;
+        if (STAGED) {
+            row1 = stages + st * N;
+            row2 = row1 + ROW;
+            ok = fmbar_wait(full0 + 8u * st, (unsigned)(it >> 1) & 1u, a.wait_limit);
+        } else {
+            row1 = a.in + ((long long)k * a.H + r1) * a.W;
+            row2 = a.in + ((long long)k * a.H + r2) * a.W;
+        }
+        const float dv1 = (float)r1 - v0, dv2 = (float)r2 - v0;
+        const bool has2 = r2 < a.H;
+
+        // forward pass 1 (radix 10, Ns = 1) from the weighted rows, zero past
+        // the row (W <= 1280 = N / 2, so points 1280.. are zero padding)
+        float2 y[10];
+#pragma unroll
+        for (int m = 5; m < 10; ++m) y[m] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const int col = j + 256 * m;
+            float vx = 0.0f, vy = 0.0f;
+            if (col < a.W) {
+                const float du = (float)col - u0;
+                vx = row1[col] * f * rsqrtf(f2v + du * du + dv1 * dv1);
+                if (has2) vy = row2[col] * f * rsqrtf(f2v + du * du + dv2 * dv2);
+            }
+            y[m] = make_float2(vx, vy);
+        }
+        dft10<false>(y);
+        // the previous row pair's last reads of buf, and this one's reads of
+        // its stage, are done
+        if (STAGED) {
+            if (!__syncthreads_and(ok)) {
+                if (j == 0) {
+                    atomicOr(a.err, 1u);
+                    // drain with the full limit: no copy may still be
+                    // writing this CTA's shared memory when it exits
+                    for (int q = 0; q < 2; ++q)
+                        if (nis[q] > 0) fmbar_wait(full0 + 8u * q, (nis[q] - 1) & 1u, kWaitLimit);
+                }
+                return;
+            }
+            if (j == 0 && rp + 2 * stride < total) {
+                filter_issue(a, rp + 2 * stride, pairs, stages + st * N, full0 + 8u * st, ROW);
+                ++nis[st];
+            }
+        } else {
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) buf[10 * j + q] = y[q];
+        __syncthreads();
+        float2 x[16];
+        // forward pass 2 (radix 16, Ns = 10)
+        if (b16) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) x[m] = buf[j + 160 * m];
+            twiddle_by<16, false>(x, a.tw, (j % 10) * 16);
+            dft16<false>(x);
+        }
+        __syncthreads();
+        if (b16) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) buf[pad16((j / 10) * 160 + j % 10 + 10 * q)] = x[q];
+        }
+        __syncthreads();
+        if (b16) {
+            // forward pass 3 (radix 16, Ns = 160): thread j ends with X[j + 160 q]
+#pragma unroll
+            for (int m = 0; m < 16; ++m) x[m] = buf[pad16(j + 160 * m)];
+            twiddle_by<16, false>(x, a.tw, j);
+            dft16<false>(x);
+            // the kernel's spectrum (real, 1/N folded in) and the caller's scale
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float hq = __ldg(a.spec + j + 160 * q) * a.scale;
+                x[q] = make_float2(x[q].x * hq, x[q].y * hq);
+            }
+            // inverse pass 1 (radix 16, Ns = 1) on the registers
+            dft16<true>(x);
+        }
+        __syncthreads();   // everyone's pass-3 reads are done
+        if (b16) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) buf[pad16(16 * j + q)] = x[q];
+        }
+        __syncthreads();
+        // inverse pass 2 (radix 16, Ns = 16)
+        if (b16) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) x[m] = buf[pad16(j + 160 * m)];
+            twiddle_by<16, true>(x, a.tw, (j % 16) * 10);
+            dft16<true>(x);
+        }
+        __syncthreads();
+        if (b16) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) buf[pad16((j / 16) * 256 + j % 16 + 16 * q)] = x[q];
+        }
+        __syncthreads();
+        // inverse pass 3 (radix 10, Ns = 256): thread j ends with result[j + 256 q]
+#pragma unroll
+        for (int m = 0; m < 10; ++m) y[m] = buf[pad16(j + 256 * m)];
+        twiddle_by<10, true>(y, a.tw, j);
+        dft10<true>(y);
+        float *o1 = a.out + ((long long)k * a.H + r1) * a.W;
+        float *o2 = a.out + ((long long)k * a.H + r2) * a.W;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int col = j + 256 * q;
+            if (col < a.W) {
+                o1[col] = y[q].x;
+                if (has2) o2[col] = y[q].y;
+            }
+        }
+    }
+}
+
 fdk_status launch_twiddles(float2 *tw, int N, cudaStream_t s)
 {
     fdk_twiddle_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
@@ -510,6 +783,31 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long total = (long long)((H + 1) / 2) * n_views;
+    if (N == kF25N && tw) {
+        const bool staged = err && W % 4 == 0 && ((uintptr_t)in % 16) == 0;
+        auto k = staged ? fdk_filter2560_kernel<true> : fdk_filter2560_kernel<false>;
+        const int smem = (int)(sizeof(float2) * (kF25N + kF25N / 16) + (staged ? sizeof(float) * 2 * kF25N : 0));
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(e));
+            return FDK_ERR_CUDA;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        long long grid = (long long)sms * per_sm;
+        if (grid > total) grid = total;
+        if (grid < 1) return FDK_OK;
+        k<<<(unsigned)grid, 256, smem, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("filter launch failed: %s", cudaGetErrorString(e));
+            return FDK_ERR_CUDA;
+        }
+        return FDK_OK;
+    }
     if (N == kF16N && tw) {
         // rows staged by bulk copies when each row is a whole number of
         // 16-byte units starting on a 16-byte boundary

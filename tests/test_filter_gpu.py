@@ -28,7 +28,7 @@ def _raw(cfg):
 
 
 @pytest.mark.parametrize("W,H", [(64, 48), (1, 5), (33, 7), (128, 3), (1000, 4),
-                                 (1025, 3), (1248, 5), (2048, 2)])
+                                 (1025, 3), (1248, 5), (1280, 3), (1281, 2), (2048, 2)])
 def test_filter_parity_shapes(W, H):
     cfg = synth.preset("small", n_views=3, det_w=W, det_h=H, pixel=0.308 * 1248.0 / W)
     raw, mats = _raw(cfg)
@@ -55,10 +55,12 @@ def test_filter_in_place_multi_pass_and_device_matrices():
     assert torch.equal(x, y)
 
 
-def test_filter_4096_in_place_two_passes_device_matrices():
-    """Rows of 1028 pixels (the N = 4096 register-FFT kernel): 520 views in
-    two passes of views, in place, and with device matrices."""
-    cfg = synth.preset("small", n_views=520, det_w=1028, det_h=3, pixel=0.308 * 1248.0 / 1028)
+@pytest.mark.parametrize("W", [1028, 1540])
+def test_filter_register_fft_in_place_two_passes_device_matrices(W):
+    """Rows of 1028 pixels (the N = 2560 register-FFT kernel) and 1540 (N =
+    4096): 520 views in two passes of views, in place, and with device
+    matrices."""
+    cfg = synth.preset("small", n_views=520, det_w=W, det_h=3, pixel=0.308 * 1248.0 / W)
     raw, mats = _raw(cfg)
     ref = oracle.preweight_filter(raw.cpu().numpy(), mats, scale=1.0)
     x = raw.clone()
@@ -70,11 +72,13 @@ def test_filter_4096_in_place_two_passes_device_matrices():
     assert torch.equal(x, y)
 
 
-def test_filter_4096_staged_equals_unstaged_rows():
-    """Rows of 1248 pixels are copied into shared memory by bulk copies
-    (16-byte aligned rows); the same images starting 4 bytes later take the
-    direct-load variant.  Both give the same bits."""
-    cfg = synth.preset("small", n_views=5, det_w=1248, det_h=7, pixel=0.308)
+@pytest.mark.parametrize("W", [1248, 1604])
+def test_filter_register_fft_staged_equals_unstaged_rows(W):
+    """Rows of 1248 (N = 2560) and 1604 pixels (N = 4096) are copied into
+    shared memory by bulk copies (16-byte aligned rows); the same images
+    starting 4 bytes later take the direct-load variant.  Both give the same
+    bits."""
+    cfg = synth.preset("small", n_views=5, det_w=W, det_h=7, pixel=0.308 * 1248.0 / W)
     raw, mats = _raw(cfg)
     a = torch.empty_like(raw)
     fdk.fdk_preweight_filter(a, raw, mats, scale=0.5)
