@@ -475,12 +475,13 @@ fdk_filter4096_kernel(const __grid_constant__ FilterArgs a)
 // has butterfly j read x[j + (N / R) m], scale it by w^m with
 // w = exp(-+2 pi i (j mod Ns) / (Ns R)), transform, and write output q to
 // (j - j mod Ns) R + j mod Ns + q Ns -- with radices 10, 16, 16 forward
-// (strides 1, 10, 160) and 16, 16, 10 inverse (strides 1, 16, 256).  The
-// radix-10 passes have 256 butterflies, one per thread; the radix-16 passes
-// 160, on the first five warps.  The last forward pass leaves thread j with
-// X[j + 160 q], the inputs of the first inverse pass, so the spectrum
-// multiply happens in registers; the last inverse pass leaves
-// result[j + 256 q].  The first exchange is unpadded (writes at stride 10:
+// (strides 1, 10, 160) and 16, 16, 10 inverse (strides 1, 16, 256).  A CTA
+// has 160 threads, one per butterfly of the radix-16 passes; the radix-10
+// passes' 256 butterflies are j and j + 160.  (With 256 threads, three
+// warps idled through the radix-16 passes: 14% slower.)  The last forward
+// pass leaves thread j with X[j + 160 q], the inputs of the first inverse
+// pass, so the spectrum multiply happens in registers; the last inverse
+// pass leaves result[j + 256 q].  The first exchange is unpadded (writes at stride 10:
 // two wavefronts per half-warp, reads conflict-free); the others are padded
 // one float2 per 16 (conflict-free both ways).
 constexpr int kF25N = 2560;
@@ -570,7 +571,7 @@ __device__ __forceinline__ void twiddle_by(float2 (&x)[R], const float2 *__restr
 }
 
 template <bool STAGED>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(160, 3)
 fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
 {
     constexpr int N = kF25N, ROW = N / 2;
@@ -579,7 +580,6 @@ fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
     float *stages = reinterpret_cast<float *>(fsm + N + N / 16);   // 2 x (2 rows of ROW)
     __shared__ __align__(8) unsigned long long full[2];
     const int j = threadIdx.x;
-    const bool b16 = j < N / 16;                  // the radix-16 passes' butterflies
     const int pairs = (a.H + 1) / 2;
     const long long total = (long long)pairs * a.n_views;
     const long long stride = gridDim.x;
@@ -634,22 +634,30 @@ fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
         const bool has2 = r2 < a.H;
 
         // forward pass 1 (radix 10, Ns = 1) from the weighted rows, zero past
-        // the row (W <= 1280 = N / 2, so points 1280.. are zero padding)
-        float2 y[10];
+        // the row (W <= 1280 = N / 2, so points 1280.. are zero padding);
+        // butterflies j and j + 160 (< 256)
+        float2 y[10], y2[10];
 #pragma unroll
-        for (int m = 5; m < 10; ++m) y[m] = make_float2(0.0f, 0.0f);
+        for (int h = 0; h < 2; ++h) {
+            const int jb = j + 160 * h;
+            float2 (&yy)[10] = h ? y2 : y;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const int col = j + 256 * m;
-            float vx = 0.0f, vy = 0.0f;
-            if (col < a.W) {
-                const float du = (float)col - u0;
-                vx = row1[col] * f * rsqrtf(f2v + du * du + dv1 * dv1);
-                if (has2) vy = row2[col] * f * rsqrtf(f2v + du * du + dv2 * dv2);
+            for (int m = 5; m < 10; ++m) yy[m] = make_float2(0.0f, 0.0f);
+            if (jb < 256) {
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    const int col = jb + 256 * m;
+                    float vx = 0.0f, vy = 0.0f;
+                    if (col < a.W) {
+                        const float du = (float)col - u0;
+                        vx = row1[col] * f * rsqrtf(f2v + du * du + dv1 * dv1);
+                        if (has2) vy = row2[col] * f * rsqrtf(f2v + du * du + dv2 * dv2);
+                    }
+                    yy[m] = make_float2(vx, vy);
+                }
+                dft10<false>(yy);
             }
-            y[m] = make_float2(vx, vy);
         }
-        dft10<false>(y);
         // the previous row pair's last reads of buf, and this one's reads of
         // its stage, are done
         if (STAGED) {
@@ -672,22 +680,26 @@ fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
         }
 #pragma unroll
         for (int q = 0; q < 10; ++q) buf[10 * j + q] = y[q];
+        if (j + 160 < 256) {
+#pragma unroll
+            for (int q = 0; q < 10; ++q) buf[10 * (j + 160) + q] = y2[q];
+        }
         __syncthreads();
         float2 x[16];
         // forward pass 2 (radix 16, Ns = 10)
-        if (b16) {
+        {
 #pragma unroll
             for (int m = 0; m < 16; ++m) x[m] = buf[j + 160 * m];
             twiddle_by<16, false>(x, a.tw, (j % 10) * 16);
             dft16<false>(x);
         }
         __syncthreads();
-        if (b16) {
+        {
 #pragma unroll
             for (int q = 0; q < 16; ++q) buf[pad16((j / 10) * 160 + j % 10 + 10 * q)] = x[q];
         }
         __syncthreads();
-        if (b16) {
+        {
             // forward pass 3 (radix 16, Ns = 160): thread j ends with X[j + 160 q]
 #pragma unroll
             for (int m = 0; m < 16; ++m) x[m] = buf[pad16(j + 160 * m)];
@@ -703,37 +715,43 @@ fdk_filter2560_kernel(const __grid_constant__ FilterArgs a)
             dft16<true>(x);
         }
         __syncthreads();   // everyone's pass-3 reads are done
-        if (b16) {
+        {
 #pragma unroll
             for (int q = 0; q < 16; ++q) buf[pad16(16 * j + q)] = x[q];
         }
         __syncthreads();
         // inverse pass 2 (radix 16, Ns = 16)
-        if (b16) {
+        {
 #pragma unroll
             for (int m = 0; m < 16; ++m) x[m] = buf[pad16(j + 160 * m)];
             twiddle_by<16, true>(x, a.tw, (j % 16) * 10);
             dft16<true>(x);
         }
         __syncthreads();
-        if (b16) {
+        {
 #pragma unroll
             for (int q = 0; q < 16; ++q) buf[pad16((j / 16) * 256 + j % 16 + 16 * q)] = x[q];
         }
         __syncthreads();
-        // inverse pass 3 (radix 10, Ns = 256): thread j ends with result[j + 256 q]
-#pragma unroll
-        for (int m = 0; m < 10; ++m) y[m] = buf[pad16(j + 256 * m)];
-        twiddle_by<10, true>(y, a.tw, j);
-        dft10<true>(y);
+        // inverse pass 3 (radix 10, Ns = 256): butterfly jb ends with result[jb + 256 q]
         float *o1 = a.out + ((long long)k * a.H + r1) * a.W;
         float *o2 = a.out + ((long long)k * a.H + r2) * a.W;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int col = j + 256 * q;
-            if (col < a.W) {
-                o1[col] = y[q].x;
-                if (has2) o2[col] = y[q].y;
+        for (int h = 0; h < 2; ++h) {
+            const int jb = j + 160 * h;
+            if (jb < 256) {
+#pragma unroll
+                for (int m = 0; m < 10; ++m) y[m] = buf[pad16(jb + 256 * m)];
+                twiddle_by<10, true>(y, a.tw, jb);
+                dft10<true>(y);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const int col = jb + 256 * q;
+                    if (col < a.W) {
+                        o1[col] = y[q].x;
+                        if (has2) o2[col] = y[q].y;
+                    }
+                }
             }
         }
     }
@@ -793,14 +811,14 @@ fdk_status launch_filter(float *out, const float *in, const float *spec, const f
             set_error("filter: shared-memory opt-in failed: %s", cudaGetErrorString(e));
             return FDK_ERR_CUDA;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 160, smem) != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
         long long grid = (long long)sms * per_sm;
         if (grid > total) grid = total;
         if (grid < 1) return FDK_OK;
-        k<<<(unsigned)grid, 256, smem, s>>>(a);
+        k<<<(unsigned)grid, 160, smem, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error("filter launch failed: %s", cudaGetErrorString(e));
