@@ -374,16 +374,21 @@ static EncodeTiledFn tmap_encoder()
 // One map per box width (maps[0..kNumBoxW)) over nv FP32 images at base
 // (W x H x nv; the row and image strides are multiples of 16 bytes because
 // W % 4 == 0).
-static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int W, int H, int nv, int nh = 1)
+static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int W, int H, int nv, int nh = 1,
+                                       int dtype = FDK_F32)
 {
     EncodeTiledFn enc = tmap_encoder();
+    const cuuint64_t esz = dtype == FDK_F32 ? 4u : 2u;
+    const CUtensorMapDataType dt = dtype == FDK_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : dtype == FDK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t gdim[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nv};
-    const cuuint64_t gstride[2] = {(cuuint64_t)W * 4u, (cuuint64_t)W * (cuuint64_t)H * 4u};
+    const cuuint64_t gstride[2] = {(cuuint64_t)W * esz, (cuuint64_t)W * (cuuint64_t)H * esz};
     const cuuint32_t estride[3] = {1, 1, 1};
     for (int q = 0; q < kNumBoxW * nh; ++q) {
         const int m = q / nh, h = q % nh;
         const cuuint32_t box[3] = {(cuuint32_t)box_width(m), (cuuint32_t)(kBoxRows << h), 1};
-        CUresult r = enc(&maps[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), gdim,
+        CUresult r = enc(&maps[q], dt, 3, const_cast<void *>(base), gdim,
                          gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
@@ -395,9 +400,9 @@ static fdk_status encode_stage_maps_at(CUtensorMap *maps, const void *base, int 
 }
 
 // The pass's maps in the kernel parameters.
-static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv)
+static fdk_status encode_stage_maps(BpArgs &a, int W, int H, int nv, int dtype = FDK_F32)
 {
-    return encode_stage_maps_at(a.tmap, a.proj, W, H, nv, kNumBoxH);
+    return encode_stage_maps_at(a.tmap, a.proj, W, H, nv, kNumBoxH, dtype);
 }
 
 // Host matrices: the views of pass [v0, v0 + nv) whose rays run mostly along
@@ -490,7 +495,7 @@ static int adj_z_run(const Geom &g, const float *mats, int n_views)
 // to 32 views spread over the scan, and the path is taken when at least 90%
 // of its pixel boxes fit a stage (coarse voxels on a fine detector give
 // boxes too large to stage, and those views would fall back to LDG).
-static bool stage_pays(const Geom &g, const float *mats, int n_views)
+static bool stage_pays(const Geom &g, const float *mats, int n_views, int esz = 4)
 {
     const int BX = 16, BY = 16, R = 16;
     const int tx = (g.nx / 2) / BX * BX, ty = (g.ny / 2) / BY * BY, tz = (g.nz / 2) / R * R;
@@ -515,22 +520,23 @@ static bool stage_pays(const Geom &g, const float *mats, int n_views)
         if (!front || umax - umin > 4096.0 || vmax - vmin > 4096.0) continue;
         const long long i0 = (long long)floor(umin) - 1, i1 = (long long)floor(umax) + 2;
         const long long j0 = (long long)floor(vmin) - 1, j1 = (long long)floor(vmax) + 2;
-        const long long wpx = i1 - (i0 & ~3LL) + 1;
+        const long long wpx = i1 - (i0 & ~(long long)(16 / esz - 1)) + 1;
         const long long m = wpx <= 32 ? 0 : (wpx - 32 + 15) / 16;
         const long long rows8 = (j1 - j0 + kBoxRows) / kBoxRows;
-        if (m < kNumBoxW && rows8 * kBoxRows * box_width((int)m) <= kStageFloats) ++fit;
+        if (m < kNumBoxW && rows8 * kBoxRows * box_width((int)m) <= (long long)kStageFloats * 4 / esz) ++fit;
     }
     return tried > 0 && fit * 10 >= tried * 9;
 }
 
-// What FDK_FETCH_AUTO resolves to the staged path for: FP32, tile 0, rows of
-// a multiple of 16 bytes, 16-byte aligned images, host matrices, and a
-// geometry for which staging pays.
+// What FDK_FETCH_AUTO resolves to the staged path for: tile 0, rows of a
+// multiple of 16 bytes, 16-byte aligned images, host matrices, and a
+// geometry for which staging pays; FP32, FP16 and BF16 pixels alike.
 static bool auto_takes_stage(const Geom &g, const void *projections, const float *matrices, int n_views,
                              const fdk_opts *o)
 {
-    return o->proj_dtype == FDK_F32 && o->tile == 0 && g.W % 4 == 0 && ((uintptr_t)projections) % 16 == 0 &&
-           !o->matrices_on_device && tmap_encoder() && stage_pays(g, matrices, n_views);
+    const int esz = (int)dtype_size(o->proj_dtype);
+    return o->tile == 0 && g.W % (16 / esz) == 0 && ((uintptr_t)projections) % 16 == 0 &&
+           !o->matrices_on_device && tmap_encoder() && stage_pays(g, matrices, n_views, esz);
 }
 
 // One device word per device, set by a bounded wait that gave up.
@@ -728,10 +734,12 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
     if ((st = check_matrices(matrices, n_views, o->matrices_on_device))) return st;
     if (o->fetch == FDK_FETCH_STAGE) {
         // the staged path's own requirements, checked before any CUDA call
-        if (o->proj_dtype != FDK_F32) return fail(FDK_ERR_UNSUPPORTED, "the staged path takes FP32 projections");
         if (o->tile != 0) return fail(FDK_ERR_INVALID_ARG, "the staged path uses tile 0");
-        if (g.W % 4 != 0 || ((uintptr_t)projections) % 16 != 0)
-            return fail(FDK_ERR_UNSUPPORTED, "the staged path needs W % 4 == 0 and 16-byte aligned projections");
+        const int esz = (int)dtype_size(o->proj_dtype);
+        if (g.W % (16 / esz) != 0 || ((uintptr_t)projections) % 16 != 0)
+            return fail(FDK_ERR_UNSUPPORTED,
+                        "the staged path needs rows of a multiple of 16 bytes (W % 4 == 0 for FP32, W % 8 == 0 "
+                        "for FP16 / BF16) and 16-byte aligned projections");
     }
     if ((st = check_device_ptr(volume, "volume"))) return st;
     if ((st = check_device_ptr(projections, "projections"))) return st;
@@ -795,7 +803,7 @@ fdk_status fdk_backproject(float *volume, const int32_t dims[3], const float vox
         a.quads = nullptr;
         a.qpitch = g.W + 3;
         a.qplane = (long long)(g.W + 3) * (g.H + 3);
-        if (use_stage && (st = encode_stage_maps(a, g.W, g.H, nv))) return st;
+        if (use_stage && (st = encode_stage_maps(a, g.W, g.H, nv, o->proj_dtype))) return st;
         if (use_tex) {
             for (int k = 0; k < nv; ++k) {
                 const char *src = static_cast<const char *>(a.proj) + (size_t)k * plane * esz;

@@ -12,7 +12,7 @@ fdk_status launch_bp_tex_bf16(const BpArgs &a, int tile, cudaStream_t s);
 fdk_status launch_bp_quad_f32(const BpArgs &a, int tile, cudaStream_t s);
 fdk_status launch_bp_quad_f16(const BpArgs &a, int tile, cudaStream_t s);
 fdk_status launch_bp_quad_bf16(const BpArgs &a, int tile, cudaStream_t s);
-fdk_status launch_bp_stage_f32(const BpArgs &a, cudaStream_t s);
+fdk_status launch_bp_stage(const BpArgs &a, int dtype, cudaStream_t s);
 
 fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile, cudaStream_t s)
 {
@@ -22,11 +22,7 @@ fdk_status launch_backproject(const BpArgs &a, int fetch, int dtype, int tile, c
     }
     switch (fetch) {
     case FDK_FETCH_STAGE:
-        if (dtype != FDK_F32) {
-            set_error("the staged path takes FP32 projections");
-            return FDK_ERR_UNSUPPORTED;
-        }
-        return launch_bp_stage_f32(a, s);
+        return launch_bp_stage(a, dtype, s);
     case FDK_FETCH_TEX:
         return dtype == FDK_F32 ? launch_bp_tex_f32(a, tile, s)
              : dtype == FDK_F16 ? launch_bp_tex_f16(a, tile, s) : launch_bp_tex_bf16(a, tile, s);

@@ -66,7 +66,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 // Called by one thread.  tmaps holds NH maps per box width, of boxes 8, 16,
 // .., 8 * 2^(NH-1) rows high: the box's rows8 8-row blocks go in as few copies
 // as those heights allow (one copy per set bit of rows8, tallest first).
-template <int NH, class A>
+// ESZ: bytes per pixel (4 for FP32 images, 2 for FP16 / BF16).
+template <int NH, class A, int ESZ = 4>
 __device__ __forceinline__ void stage_issue(const A &a, const CUtensorMap *tmaps, int v0, int lv,
                                             const int4 *sbox, float *stages, uint32_t full0, unsigned st)
 {
@@ -76,7 +77,7 @@ __device__ __forceinline__ void stage_issue(const A &a, const CUtensorMap *tmaps
     const int4 b = sbox[lv];                       // (x0, j0, m, rows8)
     const int BW = box_width(b.z);
     const uint32_t bar = full0 + 8u * st;
-    const uint32_t bytes = (uint32_t)(b.w * kBoxRows * BW) * 4u;
+    const uint32_t bytes = (uint32_t)(b.w * kBoxRows * BW) * (uint32_t)ESZ;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(bar), "r"(bytes) : "memory");
     const uint32_t dst = smem_addr(stages + (size_t)st * kStageFloats);
@@ -89,7 +90,7 @@ __device__ __forceinline__ void stage_issue(const A &a, const CUtensorMap *tmaps
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                 " [%0], [%1, {%2, %3, %4}], [%5];"
-                :: "r"(dst + (uint32_t)(r * kBoxRows * BW) * 4u), "l"(map), "r"(b.x),
+                :: "r"(dst + (uint32_t)(r * kBoxRows * BW) * (uint32_t)ESZ), "l"(map), "r"(b.x),
                    "r"(b.y + r * kBoxRows), "r"(img), "r"(bar)
                 : "memory");
             r += 1 << h;
@@ -115,15 +116,55 @@ __device__ __forceinline__ float lds_next(uint32_t addr)
     return v;
 }
 
+// The same for each pixel type: the pixel at a 32-bit shared address and the
+// one after it, widened to FP32 exactly.
+template <typename T> struct StagedPixel;
+template <> struct StagedPixel<float> {
+    static constexpr int kShift = 2;   // log2 of the pixel's bytes
+    static __device__ __forceinline__ float at(uint32_t addr) { return lds(addr); }
+    static __device__ __forceinline__ float next(uint32_t addr) { return lds_next(addr); }
+};
+template <> struct StagedPixel<__nv_bfloat16> {
+    static constexpr int kShift = 1;
+    static __device__ __forceinline__ float at(uint32_t addr)
+    {
+        unsigned v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(addr));
+        return __uint_as_float(v << 16);
+    }
+    static __device__ __forceinline__ float next(uint32_t addr)
+    {
+        unsigned v;
+        asm volatile("ld.shared.u16 %0, [%1+2];" : "=r"(v) : "r"(addr));
+        return __uint_as_float(v << 16);
+    }
+};
+template <> struct StagedPixel<__half> {
+    static constexpr int kShift = 1;
+    static __device__ __forceinline__ float at(uint32_t addr)
+    {
+        unsigned short v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+        return __half2float(__ushort_as_half(v));
+    }
+    static __device__ __forceinline__ float next(uint32_t addr)
+    {
+        unsigned short v;
+        asm volatile("ld.shared.u16 %0, [%1+2];" : "=h"(v) : "r"(addr));
+        return __half2float(__ushort_as_half(v));
+    }
+};
+
 // Staged view: the taps come from the stage's box, BW = e.o.w pixels wide,
 // whose cell (U, V) sits at index e.o.z - 2^23.  No bounds checks: the box
 // holds every tap of the tile, with zeros where it extends past the image.
 // Each f32x2 pair holds one quantity for two z neighbours, so every packed
 // operation finds its operands in place.
-template <int R>
+template <int R, typename T = float>
 __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e, float dxf, float dyf,
                                             const float *stage)
 {
+    using P = StagedPixel<T>;
     const float2 BU = f2(fmaf(dyf, e.b.x, fmaf(dxf, e.a.z, e.a.x)));
     const float2 BV = f2(fmaf(dyf, e.b.y, fmaf(dxf, e.a.w, e.a.y)));
     const float2 BW = f2(fmaf(dyf, e.w.z, fmaf(dxf, e.w.y, e.w.x)));
@@ -132,8 +173,8 @@ __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e,
     const float2 PITCH = f2(e.o.w), OZ = f2(e.o.z);
     // 32-bit shared addresses of the tap rows j and j + 1, with the index
     // magic folded into the bases
-    const uint32_t sbase = smem_addr(stage) - (kIndexBits << 2);
-    const uint32_t sbase1 = sbase + ((uint32_t)(int)e.o.w << 2);
+    const uint32_t sbase = smem_addr(stage) - (kIndexBits << P::kShift);
+    const uint32_t sbase1 = sbase + ((uint32_t)(int)e.o.w << P::kShift);
     // (u', v', w) of the run's first two voxels, then stepped two voxels at a
     // time (the steps 2 g are exact)
     const float2 RF0 = f2((float)(-R / 2), (float)(1 - R / 2));
@@ -153,10 +194,10 @@ __device__ __forceinline__ void view_staged(float (&acc)[R], const ViewEntry &e,
         const float2 flv = __fadd2_rn(__fadd2_rd(v, M), NM);
         const float2 au = __ffma2_rn(flu, NEG, u), bv = __ffma2_rn(flv, NEG, v);
         const float2 k = __fadd2_rn(__ffma2_rn(flv, PITCH, flu), OZ);
-        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << 2, o1 = (uint32_t)__float_as_int(k.y) << 2;
+        const uint32_t o0 = (uint32_t)__float_as_int(k.x) << P::kShift, o1 = (uint32_t)__float_as_int(k.y) << P::kShift;
         const uint32_t a0 = sbase + o0, a1 = sbase + o1, b0 = sbase1 + o0, b1 = sbase1 + o1;
-        const float2 p00 = f2(lds(a0), lds(a1)), p10 = f2(lds_next(a0), lds_next(a1));
-        const float2 p01 = f2(lds(b0), lds(b1)), p11 = f2(lds_next(b0), lds_next(b1));
+        const float2 p00 = f2(P::at(a0), P::at(a1)), p10 = f2(P::next(a0), P::next(a1));
+        const float2 p01 = f2(P::at(b0), P::at(b1)), p11 = f2(P::next(b0), P::next(b1));
         const float2 lo = __ffma2_rn(au, __ffma2_rn(p00, NEG, p10), p00);
         const float2 hi = __ffma2_rn(au, __ffma2_rn(p01, NEG, p11), p01);
         const float2 val = __ffma2_rn(bv, __ffma2_rn(lo, NEG, hi), lo);
@@ -207,7 +248,7 @@ __device__ __forceinline__ void stage_init(StageBarriers &sb)
 // this.  Returns false, with the tile unwritten, when a bounded wait gave up
 // (the CTA must then stop using the stages); *err is set and the copies in
 // flight are drained.
-template <int BX, int BY, int WX, int R, bool FIDX, int NH, class A>
+template <int BX, int BY, int WX, int R, bool FIDX, int NH, class A, typename T = float>
 __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps, unsigned *err, long long wait_limit,
                                            int x0, int y0, int z0, StageTables &t, StageBarriers &sb,
                                            float *stages)
@@ -223,7 +264,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
     const int ly = (warp / WPX) * WY + (lane / WX);
     const float dxf = (float)(lx - BX / 2), dyf = (float)(ly - BY / 2);
     const int W = a.g.W, H = a.g.H;
-    const float *proj = static_cast<const float *>(a.proj);
+    const T *proj = static_cast<const T *>(a.proj);
     const uint32_t full0 = smem_addr(sb.full);
 
     float acc[R];
@@ -233,7 +274,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
     unsigned base = sb.consumed;   // staged views of earlier chunks and tiles (uniform)
     for (int v0 = 0; v0 < a.n_views; v0 += KCHUNK) {
         const int nv = min(KCHUNK, a.n_views - v0);
-        build_view_table<BX, BY, R, A, true>(a, v0, nv, x0, y0, z0, t.tab, t.cls, t.act, &t.n_act,
+        build_view_table<BX, BY, R, A, true, (int)sizeof(T)>(a, v0, nv, x0, y0, z0, t.tab, t.cls, t.act, &t.n_act,
                                              nullptr, nullptr, t.sbox);
         const int n = t.n_act;
         if (warp == 0) {
@@ -252,7 +293,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
                 // the first copies of the chunk
                 for (int k = 0; k < kStages && k < count; ++k) {
                     const unsigned st = (base + k) % kStages;
-                    stage_issue<NH>(a, tmaps, v0, t.stg[k], t.sbox, stages, full0, st);
+                    stage_issue<NH, A, (int)sizeof(T)>(a, tmaps, v0, t.stg[k], t.sbox, stages, full0, st);
                     ++sb.nissue[st];
                 }
             }
@@ -268,7 +309,7 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
                 const unsigned st = slot % kStages;
                 if (!mbar_wait(full0 + 8u * st, (slot / kStages) & 1u, wait_limit)) sb.failed = 1u;
                 const ViewEntry e = t.tab[lv];
-                view_staged<R>(acc, e, dxf, dyf, stages + (size_t)st * kStageFloats);
+                view_staged<R, T>(acc, e, dxf, dyf, stages + (size_t)st * kStageFloats);
                 ++kst;
                 __syncthreads();
                 if (sb.failed) {
@@ -284,17 +325,17 @@ __device__ __forceinline__ bool stage_tile(const A &a, const CUtensorMap *tmaps,
                 if (tid == 0) {
                     const unsigned nk = kst - 1 + kStages;
                     if (nk < ns) {
-                        stage_issue<NH>(a, tmaps, v0, t.stg[nk], t.sbox, stages, full0, st);
+                        stage_issue<NH, A, (int)sizeof(T)>(a, tmaps, v0, t.stg[nk], t.sbox, stages, full0, st);
                         ++sb.nissue[st];
                     }
                 }
                 continue;
             }
             const ViewEntry e = t.tab[lv];
-            const float *img = proj + (long long)a.vidx[v0 + lv] * a.plane;
-            if (c == kInterior) view_interior_ldg<R, float, FIDX>(acc, e, dxf, dyf, img, W);
-            else if (c == kBoundary) view_checked_ldg<R, float, false>(acc, e, dxf, dyf, img, W, H);
-            else view_checked_ldg<R, float, true>(acc, e, dxf, dyf, img, W, H);
+            const T *img = proj + (long long)a.vidx[v0 + lv] * a.plane;
+            if (c == kInterior) view_interior_ldg<R, T, FIDX>(acc, e, dxf, dyf, img, W);
+            else if (c == kBoundary) view_checked_ldg<R, T, false>(acc, e, dxf, dyf, img, W, H);
+            else view_checked_ldg<R, T, true>(acc, e, dxf, dyf, img, W, H);
         }
         base += ns;
         __syncthreads();   // the next chunk overwrites the table

@@ -61,8 +61,8 @@ __device__ __forceinline__ void add_to_column(float *col, long long sxy, int z0,
 // With STAGE, interior and boundary views whose tap box fits a shared-memory
 // stage become kStaged: sbox[lv] = (x0, j0, m, rows8) describes the TMA copy
 // (columns x0.. of box width m, 8-row boxes from row j0; x0 is a multiple of
-// 4 so the first column is 16-byte aligned) and e.o.z, e.o.w address taps in
-// that box.  The box spans the corner footprint widened by one pixel on each
+// 16 / ESZ, ESZ the pixel's bytes, so the first column is 16-byte aligned)
+// and e.o.z, e.o.w address taps in that box.  The box spans the corner footprint widened by one pixel on each
 // side against FP32 rounding; it may extend past the image, where the copy
 // reads zeros -- exactly the zero-outside rule of the interpolation.
 // With bbox != nullptr it also stores, per view, the pixel box that holds
@@ -71,7 +71,7 @@ __device__ __forceinline__ void add_to_column(float *col, long long sxy, int z0,
 // to about 1e-5 pixel) and clipped to the image, and in wrange the
 // smallest and largest w of the tile's corners (of the whole tile, since w
 // is linear in the voxel position).
-template <int BX, int BY, int R, class A, bool STAGE = false>
+template <int BX, int BY, int R, class A, bool STAGE = false, int ESZ = 4>
 __device__ void build_view_table(const A &a, int v0, int nv, int x0, int y0, int z0,
                                  ViewEntry *tab, unsigned char *cls, unsigned short *act,
                                  int *n_act, int4 *bbox = nullptr, float2 *wrange = nullptr,
@@ -168,11 +168,11 @@ __device__ void build_view_table(const A &a, int v0, int nv, int x0, int y0, int
             const float lim = 1048576.0f;
             const int i0 = (int)floorf(fmaxf(umin, -lim)) - 1, i1 = (int)floorf(fminf(umax, lim)) + 2;
             const int j0 = (int)floorf(fmaxf(vmin, -lim)) - 1, j1 = (int)floorf(fminf(vmax, lim)) + 2;
-            const int bx0 = i0 & ~3;
+            const int bx0 = i0 & ~(16 / ESZ - 1);
             const int wpx = i1 - bx0 + 1;
             const int m = wpx <= 32 ? 0 : (wpx - 32 + 15) / 16;
             const int rows8 = (j1 - j0 + kBoxRows) / kBoxRows;
-            if (m < kNumBoxW && rows8 * kBoxRows * box_width(m) <= kStageFloats) {
+            if (m < kNumBoxW && rows8 * kBoxRows * box_width(m) <= kStageFloats * 4 / ESZ) {
                 const int BW = box_width(m);
                 e.o.z = (float)(((int)Vf - j0) * BW + ((int)Uf - bx0)) + kIndexMagic;
                 e.o.w = (float)BW;

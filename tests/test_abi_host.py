@@ -139,9 +139,10 @@ def test_microbench_validates_before_cuda():
 
 
 def test_staged_fetch_checks_before_cuda():
-    """The staged path's own requirements are checked on the host: FP32 only,
-    tile 0 only, W a multiple of 4 and a 16-byte aligned image base."""
-    for field, val, kw, msg in [("proj_dtype", fdk.FDK_BF16, {}, "FP32"),
+    """The staged path's own requirements are checked on the host: tile 0
+    only, rows of a multiple of 16 bytes (W a multiple of 4 for FP32, of 8 for
+    BF16 / FP16) and a 16-byte aligned image base."""
+    for field, val, kw, msg in [("proj_dtype", fdk.FDK_BF16, dict(det=(12, 8)), "W % 8"),
                                 ("tile", 2, {}, "tile 0"),
                                 (None, None, dict(det=(10, 8)), "W % 4")]:
         o = fdk.fdk_opts()

@@ -100,6 +100,24 @@ def test_full_128_cube_496_views():
     _check(s, "fdk128")
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_half_storage_staged_equals_ldg_and_oracle(dtype):
+    """16-bit images are staged as 16-bit boxes (half the bytes, twice the
+    pixels per stage) and widened to FP32 on each tap read: the result equals
+    the LDG path's on the same stored values bit for bit, and the oracle's
+    given those values within the accuracy bar; AUTO stages them."""
+    s = synth.make_scan(synth.preset("fdk512", nx=96, ny=80, nz=64, n_views=40, seed=71), device="cuda")
+    p16 = s["proj"].to(dtype)
+    got = _bp(s, fdk.FETCH_STAGE, proj=p16)
+    ldg = _bp(s, fdk.FETCH_LDG, proj=p16, tile=LDG_SAME_TILE)
+    assert torch.equal(got, ldg), float((got - ldg).abs().max())
+    auto = _bp(s, fdk.FETCH_AUTO, proj=p16)
+    assert torch.equal(got, auto)
+    ref = oracle.backproject(p16.float().cpu().numpy(), s["mats"], s["dims"], s["voxel_size"], s["origin"],
+                             threads=NCPU)
+    assert_parity(ref, got.cpu().numpy(), what=f"staged {dtype}")
+
+
 def test_512_cube_equals_ldg_bitwise():
     """The 512^3 x 496-view workload: the staged result equals the LDG
     result with the same tiles bit for bit, and its sampled parity against
@@ -168,8 +186,10 @@ def test_rejections():
     args = (s["mats"], s["voxel_size"], s["origin"])
     with pytest.raises(fdk.FdkError, match="tile 0"):
         fdk.fdk_backproject(vol, s["proj"], *args, fetch=fdk.FETCH_STAGE, tile=2)
-    with pytest.raises(fdk.FdkError, match="FP32"):
-        fdk.fdk_backproject(vol, s["proj"].to(torch.bfloat16), *args, fetch=fdk.FETCH_STAGE)
+    s68 = synth.make_scan(synth.preset("small", nx=8, ny=8, nz=8, det_w=68), device="cuda")
+    with pytest.raises(fdk.FdkError, match="W % 8"):               # 16-bit rows of 136 bytes
+        fdk.fdk_backproject(vol, s68["proj"].to(torch.bfloat16), s68["mats"], s68["voxel_size"], s68["origin"],
+                            fetch=fdk.FETCH_STAGE)
     flat = torch.zeros(s["proj"].numel() + 1, device="cuda")
     shifted = flat[1:].view(s["proj"].shape)          # 4-byte but not 16-byte aligned
     shifted.copy_(s["proj"])
