@@ -71,8 +71,9 @@ typedef enum fdk_dtype {
 } fdk_dtype;
 
 /* How the four taps are fetched.  AUTO picks the fastest path measured on
- * GB300: STAGE where it applies (FP32 projections, W a multiple of 4, a
- * 16-byte aligned base, tile 0, host matrices) and where the footprints of
+ * GB300: STAGE where it applies (rows of a multiple of 16 bytes -- W a
+ * multiple of 4 for FP32, of 8 for FP16 / BF16 --, a 16-byte aligned base,
+ * tile 0, host matrices) and where the footprints of
  * its 16 x 16 x 16 voxel tiles fit its shared-memory stages (judged on the tile
  * at the volume centre for up to 32 views; e.g. 0.5 mm voxels on 0.308 mm
  * pixels at magnification 2), LDG otherwise.  STAGE gives the same bits as
@@ -87,8 +88,10 @@ typedef enum fdk_fetch {
                                   cached staging buffer: 16 B per pixel (FP32), 8 B (FP16/BF16) */
     FDK_FETCH_STAGE = 4        /* per (tile, view) the footprint is copied into shared memory
                                   by the tensor-memory accelerator (zeros outside the image)
-                                  and the taps read from there; FP32 projections with W a
-                                  multiple of 4 and a 16-byte aligned base, opts->tile 0 (the
+                                  and the taps read from there (16-bit images as 16-bit boxes,
+                                  widened to FP32 per tap); rows of a multiple of 16 bytes
+                                  (W % 4 == 0 for FP32, W % 8 == 0 for FP16 / BF16) and a
+                                  16-byte aligned base, opts->tile 0 (the
                                   path's own 16 x 16 x 16 tiles), host or device matrices; no
                                   staging memory.  A bounded wait that gives up is reported by
                                   fdk_device_status() */
