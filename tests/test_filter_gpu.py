@@ -28,7 +28,8 @@ def _raw(cfg):
 
 
 @pytest.mark.parametrize("W,H", [(64, 48), (1, 5), (33, 7), (128, 3), (1000, 4),
-                                 (1025, 3), (1248, 5), (1280, 3), (1281, 2), (2048, 2)])
+                                 (1025, 3), (1248, 5), (1280, 3), (1281, 2), (2048, 2),
+                                 (2049, 2), (3072, 2), (4096, 2)])
 def test_filter_parity_shapes(W, H):
     cfg = synth.preset("small", n_views=3, det_w=W, det_h=H, pixel=0.308 * 1248.0 / W)
     raw, mats = _raw(cfg)

@@ -71,8 +71,10 @@ def fine():
 
 
 @pytest.mark.parametrize("fetch,tile", [(fdk.FETCH_AUTO, 0), (fdk.FETCH_LDG, 0), (fdk.FETCH_LDG, LDG_SAME_TILE),
-                                        (fdk.FETCH_TEX, 0)])
+                                        (fdk.FETCH_TEX, 0), (fdk.FETCH_STAGE, 0)])
 def test_coarse_volume(coarse, fetch, tile):
+    """FETCH_STAGE here runs the staged kernel with most boxes too large for
+    a stage, so its views fall back to its own direct reads."""
     got = _bp(coarse, fetch=fetch, tile=tile).cpu().numpy()
     rel, p = assert_parity(coarse["ref"], got, what=f"fetch {fetch} tile {tile}")
     print(f"fetch {fetch} tile {tile}: max|diff|/max|f| {rel:.3e}, PSNR {p:.1f} dB")
@@ -120,6 +122,11 @@ def test_fine_volume_staged(fine):
     assert torch.equal(staged, _bp(fine))
     rel, p = assert_parity(_oracle(fine), staged.cpu().numpy(), what="staged")
     print(f"staged: max|diff|/max|f| {rel:.3e}, PSNR {p:.1f} dB")
+    for dtype in (torch.bfloat16, torch.float16):
+        p16 = fine["proj"].to(dtype)
+        s16 = _bp(fine, proj=p16, fetch=fdk.FETCH_STAGE)
+        assert torch.equal(s16, _bp(fine, proj=p16, fetch=fdk.FETCH_LDG, tile=LDG_SAME_TILE)), dtype
+        assert_parity(_oracle(fine, p16), s16.cpu().numpy(), what=f"staged {dtype}")
 
 
 def test_adjoint(coarse, fine):
