@@ -56,7 +56,7 @@ extern "C" {
 typedef enum fdk_status {
     FDK_OK = 0,
     FDK_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype or option; nothing enqueued */
-    FDK_ERR_UNSUPPORTED = 2,   /* valid request this build cannot serve (e.g. fetch path) */
+    FDK_ERR_UNSUPPORTED = 2,   /* valid request the library cannot serve (e.g. fetch path) */
     FDK_ERR_OOM = 3,           /* a library-side allocation failed */
     FDK_ERR_CUDA = 4,          /* a CUDA runtime call failed; see fdk_last_error() */
     FDK_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */
