@@ -34,6 +34,16 @@
  * device on first use.  Calls enqueue kernels on opts->stream and return;
  * asynchronous faults surface at the caller's next synchronisation.
  *
+ * Sizes: W * (H + 1) < 2^31 cells per image, nx * ny * nz <= 2^40 voxels and
+ * W * H * n_views <= 2^40 pixels; every offset into the volume and the image
+ * stack is 64-bit (volumes past 2^31 voxels are supported).  On images of
+ * 2^23 cells or more the direct-read paths form tap indices in integers
+ * instead of FP32, with the same results.  The tile counts along y and z
+ * (tiles of 4 to 16 voxels; on the staged path also along x) go in the CUDA
+ * grid's y and z dimensions, at most 65535 each: a volume beyond that (from
+ * 262,141 voxels along one of those axes with the smallest tiles) makes the
+ * launch return FDK_ERR_CUDA.
+ *
  * Errors: argument problems return FDK_ERR_INVALID_ARG before anything is
  * enqueued; fdk_last_error() then gives a message (thread-local).  No C++
  * exception crosses this boundary.
