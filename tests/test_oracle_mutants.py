@@ -53,6 +53,13 @@ MUTANTS = {
     "count keeps pairs behind the source": ("if (!(w > 0.0)) continue;", "if (w == 0.0) continue;"),
     "count on [0, W) x [0, H)": ("if (u > -1.0 && u < Wd && v > -1.0 && v < Hd) ++count;",
                                  "if (u >= 0.0 && u < Wd && v >= 0.0 && v < Hd) ++count;"),
+    "v fraction sign": ("*b = v - fv;", "*b = fv - v;"),
+    "tap (i+1, j+1) read as (i, j+1)": ("double p11 = oracle_tap(img, jb->W, jb->H, i + 1, j + 1);",
+                                        "double p11 = oracle_tap(img, jb->W, jb->H, i, j + 1);"),
+    "adjoint drops the last column": ("if (ms[t] < 0 || ms[t] >= jb->W ||", "if (ms[t] < 0 || ms[t] >= jb->W - 1 ||"),
+    "filter convolution one-sided": ("for (int64_t mp = 0; mp < W; ++mp) {", "for (int64_t mp = 0; mp <= m; ++mp) {"),
+    "voxel list reads row j for row j+1": ("(1.0 - a) * oracle_tap(img, W, H, i, j + 1)",
+                                           "(1.0 - a) * oracle_tap(img, W, H, i, j)"),
 }
 
 
