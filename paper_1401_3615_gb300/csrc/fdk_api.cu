@@ -445,9 +445,10 @@ constexpr int kAdjPatchAlongX = 2, kAdjPatchAlongY = 16;
 //    margins and 4-pixel widening, fits half the shared buffer (8192 cells)
 //    for at least 90% of up to 32 views spread over the scan, so that the
 //    double-buffered splat keeps one barrier per view.
-// Measured on 512^3 x 496 views of 1248 x 960: 62.1 ms against 68.5 ms with
-// the 8-voxel run; at 256^3 (1 mm voxels, boxes of about 14k cells) the
-// 16-voxel run was slower, 8.27 ms against 7.18 ms.
+// Measured when the choice was made, on 512^3 x 496 views of 1248 x 960: the
+// 16-voxel run took 9% less time than the 8-voxel run (62.1 against 68.5
+// ms); at 256^3 (1 mm voxels, boxes of about 14k cells) it took 15% more
+// (8.27 against 7.18 ms).
 static int adj_z_run(const Geom &g, const float *mats, int n_views)
 {
     double wlo = 1e300, whi = -1e300;
@@ -994,7 +995,7 @@ fdk_status fdk_backproject_host(float *volume, const int32_t dims[3], const floa
     // under the back-projection of the chunk before it, half as large, while
     // the host link moves a view in less than half the time a view's
     // back-projection takes.  Every extra chunk costs a pass over the volume
-    // (about 0.6 ms at 512^3), so there are few: 31, 62, 124 and 279 views
+    // (about 0.25 ms at 512^3), so there are few: 31, 62, 124 and 279 views
     // for 496.
     std::vector<int> sizes;
     if (n_views >= 64) {
