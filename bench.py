@@ -702,15 +702,18 @@ def _batched_leg(args, cfgs, label: str, steps: int) -> dict:
 
 
 def _batched_workloads(args):
+    """The two batched workloads; a count of 0 leaves that workload out."""
     import synth
-    return [
-        (f"uneven_{args.batch_scans}_scans", synth.batch_scan_configs(args.batch_scans),
-         f"{args.batch_scans} seeded scans: volumes 64..384 per axis, 120..496 views, detectors "
-         "640x480..1248x960, FP32 (each fills the GPU alone)"),
-        (f"small_{args.small_batch_scans}_scans", synth.small_batch_scan_configs(args.small_batch_scans),
-         f"{args.small_batch_scans} seeded small scans: volumes 32..96 per axis, 60..180 views, detectors "
-         "320x240..640x480, FP32 (each under-fills the GPU alone)"),
-    ]
+    out = []
+    if args.batch_scans > 0:
+        out.append((f"uneven_{args.batch_scans}_scans", synth.batch_scan_configs(args.batch_scans),
+                    f"{args.batch_scans} seeded scans: volumes 64..384 per axis, 120..496 views, detectors "
+                    "640x480..1248x960, FP32 (each fills the GPU alone)"))
+    if args.small_batch_scans > 0:
+        out.append((f"small_{args.small_batch_scans}_scans", synth.small_batch_scan_configs(args.small_batch_scans),
+                    f"{args.small_batch_scans} seeded small scans: volumes 32..96 per axis, 60..180 views, "
+                    "detectors 320x240..640x480, FP32 (each under-fills the GPU alone)"))
+    return out
 
 
 def run_batched(args):
@@ -719,7 +722,10 @@ def run_batched(args):
     import torch
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    legs = [_batched_leg(args, cfgs, label, args.steps) for _key, cfgs, label in _batched_workloads(args)]
+    work = _batched_workloads(args)
+    if not work:
+        raise SystemExit("--batched needs --batch-scans or --small-batch-scans above 0")
+    legs = [_batched_leg(args, cfgs, label, args.steps) for _key, cfgs, label in work]
     main = legs[0]
     line = {
         "metric": "GUp/s, scans of uneven size in one persistent launch (batched form)",
